@@ -1,0 +1,152 @@
+/*
+ * knnjoin.h -- C ABI of the B300 exact K-nearest-neighbour self-join.
+ *
+ * The operation (Gowanlock, "Hybrid KNN-Join", Sec. 2.1, problem statement):
+ * for every point p_i of a data set D of n points in d dimensions, find its K
+ * nearest neighbours under the Euclidean distance, the point itself excluded.
+ * This library computes it on one GPU with the paper's GPU method -- a grid
+ * index built on the device (Sec. 3.1, 4.5), a search distance chosen from a
+ * sampled distance histogram (Sec. 4.3), a density-ordered query work queue
+ * (Sec. 4.4, Fig. 4) and a per-query scan of the 3^n adjacent cells (Alg. 1,
+ * GPUJoinKernel) -- made exact and self-contained: a query whose K-th
+ * neighbour is not certified by the cells scanned is re-queued with a wider
+ * ring of cells (the paper re-queues failed queries, Alg. 1, Sec. 4.4) until
+ * it is.
+ *
+ * Result convention (the paper fixes neither precision nor tie order; this
+ * library fixes both):
+ *   D(i,j)  = canonical FP64 squared distance: t_k = fl64(fl64((double)x_ik -
+ *             (double)x_jk)^2), summed left to right in FP64, no fused
+ *             multiply-add;
+ *   row i   = the K indices j != i smallest under (D(i,j), j), ascending;
+ *   dist    = correctly rounded sqrt(D(i,j)) in FP64.
+ * Another point with the same coordinates as p_i is a neighbour at distance 0.
+ *
+ * Conventions common to all calls:
+ *   - Points are row-major float32 [n][d]; ids are int32 [n][K]; distances
+ *     are float64 [n][K].  Pointers may be host or device memory (detected
+ *     per call); device pointers must belong to the context's device.
+ *   - The caller owns every buffer it passes.  The library never frees or
+ *     retains them past the call (blocking calls) or past the poll that
+ *     returns a final status (submitted jobs).  The library owns its index
+ *     and scratch memory, allocated through the optional hook in
+ *     knnjoin_config, until knnjoin_destroy.
+ *   - No call aborts, exits or traps.  Errors are returned as a status; the
+ *     message is available from knnjoin_last_error.  After KNN_ERR_CUDA the
+ *     context must be destroyed.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef KNNJOIN_H
+#define KNNJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct knnjoin_ctx knnjoin_ctx;
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_ERR_INVALID = 1,    /* bad argument: see knnjoin_last_error */
+    KNN_ERR_NOMEM = 2,      /* device or host allocation failed */
+    KNN_ERR_CUDA = 3,       /* CUDA runtime error; destroy the context */
+    KNN_ERR_NOT_READY = 4,  /* submitted job still running */
+    KNN_ERR_TIMEOUT = 5,    /* a bounded wait expired */
+    KNN_ERR_CANCELLED = 6,  /* job was cancelled */
+    KNN_ERR_QUEUE_FULL = 7  /* serving queue has no free slot */
+} knnjoin_status;
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    void *stream;             /* cudaStream_t to run on; NULL = the context makes its own */
+    void *(*alloc)(size_t bytes, void *user);  /* optional device allocator */
+    void (*free)(void *ptr, void *user);       /* matching free */
+    void *user;
+    size_t hbm_budget_bytes;  /* serving admission limit; 0 = 90% of free memory */
+    int max_jobs;             /* serving queue slots; 0 = 64 */
+    const char *tune_cache_path; /* reserved */
+    float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.3); 0 = default */
+    int reserved[8];
+} knnjoin_config;
+
+/* One self-join (batched and served calls). */
+typedef struct {
+    const float *points;  /* [n][d] float32 */
+    int64_t n;
+    int d;
+    int K;
+    int32_t *out_ids;     /* [n][K] */
+    double *out_dist;     /* [n][K] */
+} knnjoin_job;
+
+/* Counters of the last join run by a context (or of a submitted job). */
+typedef struct {
+    int64_t n;
+    int d, K;
+    int passes;                    /* passes of the re-queue loop */
+    int start_level;
+    int64_t pass_queries[16];      /* active queries per pass (pass 0 = n) */
+    int64_t candidates;            /* candidate distance evaluations, all passes */
+    int64_t band_entries;          /* exact re-scores (FP64-canonical) */
+    int64_t overflow_queries;      /* queries redone with exact keys */
+    double eps_mean, eps_min;      /* Sec. 4.3 search distance */
+    double cell_width;             /* level-0 cell side */
+    int key_bits;
+    int fixed_point;               /* 1 = integer fast path for exact distances */
+    double ms_total;               /* device time of the join (events) */
+    double ms_index;               /* device time up to the first pass */
+} knnjoin_stats;
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, own stream).
+ * Returns KNN_ERR_INVALID for a bad device, KNN_ERR_CUDA if CUDA fails. */
+knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out);
+
+/* Free every resource of the context.  NULL is a no-op. */
+void knnjoin_destroy(knnjoin_ctx *ctx);
+
+/* Blocking exact KNN self-join (Sec. 2.1; method Alg. 1 / Sec. 3-4).
+ *   points   : float32 [n][d], host or device
+ *   n        : 2 <= n <= 2^31 - 1
+ *   d        : 1 <= d <= 8
+ *   K        : 1 <= K <= min(n - 1, 256)
+ *   out_ids  : int32 [n][K], host or device; row i ascending by (D, id)
+ *   out_dist : float64 [n][K], host or device; correctly rounded sqrt(D)
+ * KNN_ERR_INVALID on bad sizes, NULL pointers or a non-finite coordinate
+ * (detected on the device; the outputs are then unspecified). */
+knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                 int32_t *out_ids, double *out_dist);
+
+/* Blocking: run njobs independent self-joins (same conventions as
+ * knnjoin_self_join per job).  Returns the first failing job's status. */
+knnjoin_status knnjoin_self_join_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs, int njobs);
+
+/* Serving: enqueue a join and return at once with *job_id.  The caller keeps
+ * the job's buffers alive until knnjoin_poll returns a status other than
+ * KNN_ERR_NOT_READY.  KNN_ERR_QUEUE_FULL if no slot is free. */
+knnjoin_status knnjoin_submit(knnjoin_ctx *ctx, const knnjoin_job *job, uint64_t *job_id);
+
+/* KNN_OK when the job finished, KNN_ERR_NOT_READY while it runs, else its
+ * error.  Polling a finished job again returns KNN_ERR_INVALID. */
+knnjoin_status knnjoin_poll(knnjoin_ctx *ctx, uint64_t job_id);
+
+/* Cancel a job that has not started; a later poll returns KNN_ERR_CANCELLED. */
+knnjoin_status knnjoin_cancel(knnjoin_ctx *ctx, uint64_t job_id);
+
+/* Counters of a job (job_id 0: the last blocking join). */
+knnjoin_status knnjoin_get_stats(knnjoin_ctx *ctx, uint64_t job_id, knnjoin_stats *out);
+
+/* Message of the last error on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char *knnjoin_last_error(knnjoin_ctx *ctx);
+
+/* Library version string. */
+const char *knnjoin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNJOIN_H */

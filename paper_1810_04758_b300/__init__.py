@@ -1,0 +1,273 @@
+"""Python binding of the B300 exact KNN self-join library (libknnjoin.so).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  The functions carry the C ABI's names (include/knnjoin.h); the
+``Context`` class wraps them for torch tensors (device memory and streams come
+from PyTorch).  There is no CPU fallback: importing works without a GPU, but
+every call needs the built library and a CUDA device, and fails loudly
+otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libknnjoin.so")
+
+KNN_OK = 0
+KNN_ERR_INVALID = 1
+KNN_ERR_NOMEM = 2
+KNN_ERR_CUDA = 3
+KNN_ERR_NOT_READY = 4
+KNN_ERR_TIMEOUT = 5
+KNN_ERR_CANCELLED = 6
+KNN_ERR_QUEUE_FULL = 7
+STATUS_NAMES = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_NOMEM", 3: "KNN_ERR_CUDA",
+                4: "KNN_ERR_NOT_READY", 5: "KNN_ERR_TIMEOUT", 6: "KNN_ERR_CANCELLED",
+                7: "KNN_ERR_QUEUE_FULL"}
+
+# Every symbol include/knnjoin.h declares.
+EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_self_join_batch",
+           "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
+           "knnjoin_last_error", "knnjoin_version")
+
+
+class KnnjoinConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("user", ctypes.c_void_p),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
+                ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class KnnjoinJob(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int),
+                ("K", ctypes.c_int), ("out_ids", ctypes.c_void_p), ("out_dist", ctypes.c_void_p)]
+
+
+class KnnjoinStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int), ("K", ctypes.c_int),
+                ("passes", ctypes.c_int), ("start_level", ctypes.c_int),
+                ("pass_queries", ctypes.c_int64 * 16), ("candidates", ctypes.c_int64),
+                ("band_entries", ctypes.c_int64), ("overflow_queries", ctypes.c_int64),
+                ("eps_mean", ctypes.c_double), ("eps_min", ctypes.c_double),
+                ("cell_width", ctypes.c_double), ("key_bits", ctypes.c_int),
+                ("fixed_point", ctypes.c_int), ("ms_total", ctypes.c_double),
+                ("ms_index", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if name == "pass_queries":
+                v = [int(x) for x in v[: max(self.passes, 0)]]
+            d[name] = v
+        return d
+
+
+class KnnJoinError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libknnjoin.so (built by paper_1810_04758_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libknnjoin.so not built ({path}); run paper_1810_04758_b300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.knnjoin_create.argtypes = [ctypes.POINTER(KnnjoinConfig), ctypes.POINTER(P)]
+    lib.knnjoin_create.restype = I
+    lib.knnjoin_destroy.argtypes = [P]
+    lib.knnjoin_destroy.restype = None
+    lib.knnjoin_self_join.argtypes = [P, P, I64, I, I, P, P]
+    lib.knnjoin_self_join.restype = I
+    lib.knnjoin_self_join_batch.argtypes = [P, ctypes.POINTER(KnnjoinJob), I]
+    lib.knnjoin_self_join_batch.restype = I
+    lib.knnjoin_submit.argtypes = [P, ctypes.POINTER(KnnjoinJob), ctypes.POINTER(ctypes.c_uint64)]
+    lib.knnjoin_submit.restype = I
+    lib.knnjoin_poll.argtypes = [P, ctypes.c_uint64]
+    lib.knnjoin_poll.restype = I
+    lib.knnjoin_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.knnjoin_cancel.restype = I
+    lib.knnjoin_get_stats.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(KnnjoinStats)]
+    lib.knnjoin_get_stats.restype = I
+    lib.knnjoin_last_error.argtypes = [P]
+    lib.knnjoin_last_error.restype = ctypes.c_char_p
+    lib.knnjoin_version.argtypes = []
+    lib.knnjoin_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C ABI's names (raw pointers as Python ints)
+# ---------------------------------------------------------------------------
+def knnjoin_create(cfg: Optional[KnnjoinConfig] = None) -> int:
+    lib = load_library()
+    out = ctypes.c_void_p()
+    st = lib.knnjoin_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(out))
+    if st != KNN_OK:
+        raise KnnJoinError(st, "knnjoin_create failed")
+    return out.value
+
+
+def knnjoin_destroy(ctx: int) -> None:
+    load_library().knnjoin_destroy(ctx)
+
+
+def knnjoin_last_error(ctx: int) -> str:
+    return load_library().knnjoin_last_error(ctx).decode()
+
+
+def knnjoin_version() -> str:
+    return load_library().knnjoin_version().decode()
+
+
+def _check(ctx: int, st: int) -> int:
+    if st not in (KNN_OK, KNN_ERR_NOT_READY):
+        raise KnnJoinError(st, knnjoin_last_error(ctx))
+    return st
+
+
+def knnjoin_self_join(ctx: int, points: int, n: int, d: int, K: int, out_ids: int,
+                      out_dist: int) -> int:
+    return _check(ctx, load_library().knnjoin_self_join(ctx, points, n, d, K, out_ids, out_dist))
+
+
+def knnjoin_self_join_batch(ctx: int, jobs: list[KnnjoinJob]) -> int:
+    arr = (KnnjoinJob * len(jobs))(*jobs)
+    return _check(ctx, load_library().knnjoin_self_join_batch(ctx, arr, len(jobs)))
+
+
+def knnjoin_submit(ctx: int, job: KnnjoinJob) -> int:
+    jid = ctypes.c_uint64()
+    _check(ctx, load_library().knnjoin_submit(ctx, ctypes.byref(job), ctypes.byref(jid)))
+    return jid.value
+
+
+def knnjoin_poll(ctx: int, job_id: int) -> int:
+    """Raw status (KNN_OK / KNN_ERR_NOT_READY / error code); never raises."""
+    return load_library().knnjoin_poll(ctx, job_id)
+
+
+def knnjoin_cancel(ctx: int, job_id: int) -> int:
+    return load_library().knnjoin_cancel(ctx, job_id)
+
+
+def knnjoin_get_stats(ctx: int, job_id: int = 0) -> dict:
+    st = KnnjoinStats()
+    _check(ctx, load_library().knnjoin_get_stats(ctx, job_id, ctypes.byref(st)))
+    return st.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# torch-facing wrapper
+# ---------------------------------------------------------------------------
+class Context:
+    """A library context bound to a CUDA device and (by default) torch's
+    current stream on it."""
+
+    def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
+                 max_jobs: int = 0, hbm_budget_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self._torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        cfg = KnnjoinConfig()
+        cfg.device = device
+        cfg.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        cfg.width_mult = width_mult
+        cfg.max_jobs = max_jobs
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        self._cfg = cfg
+        self.ctx = knnjoin_create(cfg)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            knnjoin_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _outputs(self, n: int, K: int, like, out_ids, out_dist):
+        torch = self._torch
+        dev = like.device
+        if out_ids is None:
+            out_ids = torch.empty((n, K), dtype=torch.int32, device=dev)
+        if out_dist is None:
+            out_dist = torch.empty((n, K), dtype=torch.float64, device=dev)
+        for t, dt in ((out_ids, torch.int32), (out_dist, torch.float64)):
+            if t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != (n, K):
+                raise ValueError("output tensors must be contiguous [n, K] int32 / float64")
+        return out_ids, out_dist
+
+    def self_join(self, points, K: int, out_ids=None, out_dist=None):
+        """Exact KNN self-join of a float32 [n, d] tensor (host or device).
+        Returns (ids int32 [n, K], dist float64 [n, K]) on the points' device."""
+        torch = self._torch
+        if points.dtype != torch.float32 or points.dim() != 2:
+            raise ValueError("points must be a float32 [n, d] tensor")
+        points = points.contiguous()
+        n, d = points.shape
+        out_ids, out_dist = self._outputs(n, K, points, out_ids, out_dist)
+        knnjoin_self_join(self.ctx, points.data_ptr(), n, d, K, out_ids.data_ptr(),
+                          out_dist.data_ptr())
+        return out_ids, out_dist
+
+    def self_join_batch(self, point_list, Ks):
+        torch = self._torch
+        jobs, outs = [], []
+        for p, K in zip(point_list, Ks):
+            p = p.contiguous()
+            n, d = p.shape
+            ids, dist = self._outputs(n, K, p, None, None)
+            outs.append((ids, dist))
+            jobs.append(KnnjoinJob(p.data_ptr(), n, d, K, ids.data_ptr(), dist.data_ptr()))
+        self._keep = point_list
+        knnjoin_self_join_batch(self.ctx, jobs)
+        return outs
+
+    def submit(self, points, K: int, out_ids=None, out_dist=None):
+        """Enqueue a join; returns (job_id, ids, dist).  Keep the tensors alive
+        until poll() returns a final status."""
+        points = points.contiguous()
+        n, d = points.shape
+        out_ids, out_dist = self._outputs(n, K, points, out_ids, out_dist)
+        job = KnnjoinJob(points.data_ptr(), n, d, K, out_ids.data_ptr(), out_dist.data_ptr())
+        return knnjoin_submit(self.ctx, job), out_ids, out_dist
+
+    def poll(self, job_id: int) -> int:
+        return knnjoin_poll(self.ctx, job_id)
+
+    def cancel(self, job_id: int) -> int:
+        return knnjoin_cancel(self.ctx, job_id)
+
+    def stats(self, job_id: int = 0) -> dict:
+        return knnjoin_get_stats(self.ctx, job_id)
+
+    def last_error(self) -> str:
+        return knnjoin_last_error(self.ctx)

@@ -1,0 +1,120 @@
+// common.cuh -- shared definitions of the B300 KNN self-join kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "exact.cuh"
+
+namespace knn {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_DIM = 8;
+
+// Per-join parameters computed on the device (steps a1-a2) and read back.
+struct GridParams {
+    int n, d, K;
+    float lo[MAX_DIM], hi[MAX_DIM];  // bounding box (face origin = lo)
+    int fixed_ok;                    // every coordinate is X * 2^-F, |X| < 2^30
+    int F;
+    float eps_mean, eps_min;         // Sec. 4.3 search distance
+    float w0, inv_w0;                // level-0 cell side
+    int cmax0[MAX_DIM];              // largest level-0 cell index per dimension
+    int bits;                        // bits per dimension of the Morton key
+    int key_bits;                    // d * bits
+    int top_level;                   // level at which the grid is one cell
+    int start_level;                 // level of the first pass
+    int nonfinite;                   // input holds NaN / Inf
+};
+
+// Reductions of step a1 (atomics targets).
+struct PrepReduce {
+    unsigned lo_enc[MAX_DIM], hi_enc[MAX_DIM];
+    int min_lsb, max_msb;
+    int nonfinite;
+    int pad;
+    double eps_sum;
+    unsigned long long eps_pairs;
+    unsigned hist[2][1024];
+};
+
+// Order-preserving float <-> uint32 encodings (for atomicMin/Max on floats).
+__device__ __forceinline__ unsigned fenc(float f)
+{
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float fdec(unsigned u)
+{
+    unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(v);
+#else
+    return bitsf(v);
+#endif
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Level-0 cell of coordinate x: the largest c in [0, limit] whose lower face
+// fmaf(c, w, o) is <= x.  Faces are exact float values, strictly increasing in
+// c (the cell side is at least 2^-21 of the largest face magnitude), so the
+// assignment is exact and the certificate can use the very same faces.
+__device__ __forceinline__ int cell_of(float x, float o, float w, float invw, int limit)
+{
+    float f = floorf((x - o) * invw);
+    f = fminf(fmaxf(f, 0.0f), (float)limit);
+    int c = (int)f;
+    while (c > 0 && fmaf((float)c, w, o) > x) --c;
+    while (c < limit && fmaf((float)(c + 1), w, o) <= x) ++c;
+    return c;
+}
+
+__device__ __forceinline__ float face_of(int c, float o, float w)
+{
+    return fmaf((float)c, w, o);
+}
+
+// Morton interleave of d coordinates with `nb` bits each (bit b of
+// coordinate j goes to key bit b*d + j).
+__device__ __forceinline__ uint64_t morton_encode(const int *c, int d, int nb)
+{
+    uint64_t key = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < d; ++j)
+            key |= (uint64_t)((c[j] >> b) & 1) << (b * d + j);
+    return key;
+}
+
+__device__ __forceinline__ void morton_decode(uint64_t key, int d, int nb, int *c)
+{
+    for (int j = 0; j < d; ++j) c[j] = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < d; ++j)
+            c[j] |= (int)((key >> (b * d + j)) & 1) << b;
+}
+
+// Positive normal float -> IEEE double bit pattern; subnormals and zero map
+// to +0 (callers use this as a lower bound).
+__device__ __forceinline__ uint64_t f32_to_f64_bits_floor(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    uint32_t e8 = b >> 23;
+    if (e8 == 0 || (b >> 31)) return 0;
+    return ((uint64_t)(e8 - 127 + 1023) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+}
+
+}  // namespace knn

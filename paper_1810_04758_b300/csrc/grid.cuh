@@ -1,0 +1,395 @@
+// grid.cuh -- index construction on the GPU (paper Sec. 3.1, 4.3, 4.4, 4.5).
+//
+//  a1  k_prep        AoS -> SoA, bounding box, fixed-point frame, finiteness.
+//  a2  k_eps_pairs   mean distance among ~0.1% sampled points (eps_mean).
+//      k_eps_hist    histogram of sampled distances below eps_mean (n_bins
+//                    bins), twice: over [0, eps_mean), then refined over
+//                    [0, 2 x the first estimate).
+//      k_params      eps_min = middle of the first bin whose cumulative count
+//                    reaches K per sampled point; cell side, grid, key bits.
+//  a3  k_keys        exact level-0 cell of every point, Morton key.
+//  a4  radix sort (primitives.cuh).
+//  a5  k_gather      coordinates permuted to key order (SoA).
+//      k_run_flags / k_cells / k_hash_insert: the non-empty cells of a level
+//                    (a level-l cell is a run of equal key >> (d*l)) and a
+//                    hash map from cell key to its run.
+//  a6  k_group_*     density-ordered work queue: groups of queries sharing a
+//                    cell, sorted by count descending (Fig. 4), split into
+//                    work items.
+#pragma once
+#include "common.cuh"
+
+namespace knn {
+
+// ---------------------------------------------------------------------------
+// a1
+// ---------------------------------------------------------------------------
+__global__ void k_prep(const float *__restrict__ pts, int64_t n, int d, float *__restrict__ xs,
+                       PrepReduce *red)
+{
+    float lmin[MAX_DIM], lmax[MAX_DIM];
+    for (int k = 0; k < MAX_DIM; ++k) {
+        lmin[k] = __int_as_float(0x7f800000);
+        lmax[k] = -__int_as_float(0x7f800000);
+    }
+    int lsb = 1 << 30, msb = -(1 << 30), bad = 0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        for (int k = 0; k < d; ++k) {
+            float x = pts[i * d + k];
+            xs[(int64_t)k * n + i] = x;
+            if (!isfinite(x)) {
+                bad = 1;
+                continue;
+            }
+            lmin[k] = fminf(lmin[k], x);
+            lmax[k] = fmaxf(lmax[k], x);
+            if (x != 0.0f) {
+                uint32_t M;
+                int E;
+                fdecode(x, M, E);
+                lsb = min(lsb, E + (__ffs(M) - 1));
+                msb = max(msb, E + 31 - __clz(M));
+            }
+        }
+    }
+    for (int k = 0; k < d; ++k) {
+        float a = lmin[k], b = lmax[k];
+        for (int o = 16; o; o >>= 1) {
+            a = fminf(a, __shfl_xor_sync(FULL, a, o));
+            b = fmaxf(b, __shfl_xor_sync(FULL, b, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&red->lo_enc[k], fenc(a));
+            atomicMax(&red->hi_enc[k], fenc(b));
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        lsb = min(lsb, __shfl_xor_sync(FULL, lsb, o));
+        msb = max(msb, __shfl_xor_sync(FULL, msb, o));
+        bad |= __shfl_xor_sync(FULL, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&red->min_lsb, lsb);
+        atomicMax(&red->max_msb, msb);
+        if (bad) atomicOr(&red->nonfinite, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2: search distance.  Samples are taken at fixed strides (deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dist_f32(const float *xs, int64_t n, int d, int64_t i, int64_t j)
+{
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        float t = xs[(int64_t)k * n + i] - xs[(int64_t)k * n + j];
+        s = fmaf(t, t, s);
+    }
+    return sqrtf(s);
+}
+
+// Mean distance over all pairs of `sm` points at stride n / sm.
+__global__ void k_eps_pairs(const float *xs, int64_t n, int d, int64_t sm, PrepReduce *red)
+{
+    int64_t stride = n / sm;
+    float acc = 0.0f;
+    unsigned long long cnt = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < sm * sm;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = p / sm, b = p % sm;
+        if (b >= a) continue;
+        acc += dist_f32(xs, n, d, a * stride, b * stride);
+        ++cnt;
+    }
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(FULL, acc, o);
+        cnt += __shfl_xor_sync(FULL, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) {
+        atomicAdd(&red->eps_sum, (double)acc);
+        atomicAdd(&red->eps_pairs, cnt);
+    }
+}
+
+// Histogram of distances from S sample points (stride n / S) to m subset
+// points (stride n / m), bins of width range / 1024 over [0, range), where
+// range = eps_mean (stage 0) or twice the stage-0 estimate (stage 1).
+__global__ void k_eps_hist(const float *xs, int64_t n, int d, int64_t S, int64_t m,
+                           const GridParams *gp, PrepReduce *red, int stage)
+{
+    __shared__ unsigned h[1024];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    float range = stage == 0 ? gp->eps_mean : 2.0f * gp->eps_min;
+    if (range > 0.0f) {
+        float inv_bw = 1024.0f / range;
+        int64_t sstride = n / S, mstride = n / m;
+        int64_t total = S * m;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            int64_t si = (t / m) * sstride, mj = (t % m) * mstride;
+            if (si == mj) continue;
+            float dd = dist_f32(xs, n, d, si, mj);
+            if (dd < range) {
+                int b = min((int)(dd * inv_bw), 1023);
+                atomicAdd(&h[b], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+        if (h[i]) atomicAdd(&red->hist[stage][i], h[i]);
+}
+
+struct ParamsIn {
+    int64_t n;
+    int d, K;
+    int64_t S, m;        // histogram samples / subset size
+    float width_mult;    // cell side = width_mult * eps_min
+    int start_level;
+};
+
+// stage 0: eps_mean and the grid-independent fields; stage 1: eps_min
+// estimate from hist[0]; stage 2: refined eps_min from hist[1], cell side,
+// grid and key bits.
+__global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int stage)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    const int d = in.d;
+    if (stage == 0) {
+        gp->n = (int)in.n;
+        gp->d = d;
+        gp->K = in.K;
+        gp->nonfinite = red->nonfinite;
+        for (int k = 0; k < d; ++k) {
+            gp->lo[k] = fdec(red->lo_enc[k]);
+            gp->hi[k] = fdec(red->hi_enc[k]);
+        }
+        if (red->max_msb < red->min_lsb) {  // every coordinate is zero
+            gp->fixed_ok = 1;
+            gp->F = 0;
+        } else {
+            int F = -red->min_lsb;
+            gp->F = F;
+            gp->fixed_ok = (red->max_msb + F <= 29) ? 1 : 0;
+        }
+        gp->eps_mean = red->eps_pairs ? (float)(red->eps_sum / (double)red->eps_pairs) : 0.0f;
+        gp->eps_min = 0.0f;
+        return;
+    }
+    // cumulative count per sampled point reaches K (scaled to the subset)
+    const unsigned *h = red->hist[stage - 1];
+    float range = stage == 1 ? gp->eps_mean : 2.0f * gp->eps_min;
+    double target = (double)in.K * (double)in.S * (double)in.m / (double)(in.n - 1);
+    double cum = 0.0;
+    int pick = -1;
+    for (int b = 0; b < 1024; ++b) {
+        cum += h[b];
+        if (cum >= target) {
+            pick = b;
+            break;
+        }
+    }
+    float eps = pick >= 0 ? (pick + 0.5f) * (range / 1024.0f) : range;
+    if (stage == 1) {
+        gp->eps_min = eps;
+        return;
+    }
+    if (!(range > 0.0f)) eps = gp->eps_mean;
+    gp->eps_min = eps;
+
+    // cell side and grid
+    float ext = 0.0f, mag = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        ext = fmaxf(ext, gp->hi[k] - gp->lo[k]);
+        mag = fmaxf(mag, fmaxf(fabsf(gp->lo[k]), fabsf(gp->hi[k])));
+    }
+    int bmax = min(24, 63 / d);
+    float w = in.width_mult * eps;
+    if (!(w > 0.0f) || !isfinite(w)) w = ext > 0.0f ? ext : 1.0f;
+    float wf1 = ldexpf(mag, -21);                            // faces strictly increasing
+    float wf2 = ext / (float)((1 << bmax) - 4);              // grid fits the key bits
+    w = fmaxf(w, fmaxf(wf1, wf2));
+    if (!(w > 0.0f)) w = 1.0f;
+    if (!isfinite(w)) w = 3.0e38f;
+    gp->w0 = w;
+    gp->inv_w0 = 1.0f / w;
+    int cmax = 0;
+    for (int k = 0; k < d; ++k) {
+        int c = cell_of(gp->hi[k], gp->lo[k], w, gp->inv_w0, (1 << bmax) - 1);
+        gp->cmax0[k] = c;
+        cmax = max(cmax, c);
+    }
+    int bits = cmax ? 32 - __clz(cmax) : 0;
+    gp->bits = bits;
+    gp->key_bits = bits * d;
+    gp->top_level = bits;
+    gp->start_level = min(in.start_level, bits);
+}
+
+// ---------------------------------------------------------------------------
+// a3 / a5
+// ---------------------------------------------------------------------------
+__global__ void k_keys(const float *__restrict__ xs, int64_t n, const GridParams *__restrict__ gp,
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
+{
+    const int d = gp->d, bits = gp->bits;
+    const float w = gp->w0, iw = gp->inv_w0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int c[MAX_DIM];
+        for (int k = 0; k < d; ++k)
+            c[k] = cell_of(xs[(int64_t)k * n + i], gp->lo[k], w, iw, gp->cmax0[k]);
+        keys[i] = morton_encode(c, d, bits);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_gather(const float *__restrict__ xs, int64_t n, int d, const uint32_t *__restrict__ perm,
+                         float *__restrict__ xsort)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i = perm[s];
+        for (int k = 0; k < d; ++k) xsort[(int64_t)k * n + s] = xs[(int64_t)k * n + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Runs of equal key >> shift over keys[idx[a]] (idx == nullptr: identity).
+// ---------------------------------------------------------------------------
+__global__ void k_run_flags(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx,
+                            int64_t m, int shift, uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t ka = keys[idx ? idx[a] : a] >> shift;
+        uint32_t f = 1;
+        if (a > 0) f = ka != (keys[idx ? idx[a - 1] : a - 1] >> shift);
+        flags[a] = f;
+    }
+}
+
+// Run starts: begin[rid[a]] = a where flags[a]; also the run count.
+__global__ void k_run_begin(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ rid,
+                            int64_t m, uint32_t *__restrict__ begin, uint32_t *count)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[a]) begin[rid[a]] = (uint32_t)a;
+        if (a == m - 1) {
+            uint32_t c = rid[a] + flags[a];
+            *count = c;
+            begin[c] = (uint32_t)m;
+        }
+    }
+}
+
+// Hash map (open addressing, linear probing) from level cell key to its run
+// [begin, end) in key order.  Capacity is a power of two >= 2 x cells.
+constexpr uint64_t HASH_EMPTY = ~0ull;
+
+__global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
+                              const uint32_t *ncells_p, int shift, uint64_t *hkey, uint2 *hval,
+                              uint32_t hmask)
+{
+    uint32_t ncells = *ncells_p;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        uint32_t b = begin[c], e = begin[c + 1];
+        uint64_t P = keys[b] >> shift;
+        uint32_t h = (uint32_t)mix64(P) & hmask;
+        for (uint32_t probe = 0; probe <= hmask; ++probe) {
+            unsigned long long prev = atomicCAS((unsigned long long *)&hkey[h], HASH_EMPTY, P);
+            if (prev == HASH_EMPTY || prev == P) {
+                hval[h] = make_uint2(b, e);
+                break;
+            }
+            h = (h + 1) & hmask;
+        }
+    }
+}
+
+__device__ __forceinline__ uint2 hash_lookup(const uint64_t *__restrict__ hkey, const uint2 *__restrict__ hval,
+                                             uint32_t hmask, uint64_t P)
+{
+    uint32_t h = (uint32_t)mix64(P) & hmask;
+    for (uint32_t probe = 0; probe <= hmask; ++probe) {
+        uint64_t k = hkey[h];
+        if (k == P) return hval[h];
+        if (k == HASH_EMPTY) break;
+        h = (h + 1) & hmask;
+    }
+    return make_uint2(0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// a6: groups (queries of the active list sharing a level cell), ordered by
+// size descending (the paper's density order), split into work items of at
+// most `qpi` queries.
+// ---------------------------------------------------------------------------
+__global__ void k_group_sizes(const uint32_t *__restrict__ gbegin, const uint32_t *ng_p,
+                              uint32_t *__restrict__ sortkey, uint32_t *__restrict__ gid,
+                              uint32_t *maxsize)
+{
+    uint32_t ng = *ng_p;
+    uint32_t lmax = 0;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        uint32_t sz = gbegin[g + 1] - gbegin[g];
+        sortkey[g] = sz;
+        gid[g] = g;
+        lmax = max(lmax, sz);
+    }
+    for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxsize, lmax);
+}
+
+// sortkey = maxsize - size (ascending sort => size descending, stable)
+__global__ void k_group_sortkey(uint32_t *__restrict__ sortkey, const uint32_t *ng_p, const uint32_t *maxsize)
+{
+    uint32_t ng = *ng_p, mx = *maxsize;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        sortkey[g] = mx - sortkey[g];
+}
+
+__global__ void k_group_nitems(const uint32_t *__restrict__ gbegin, const uint32_t *__restrict__ order,
+                               const uint32_t *ng_p, int qpi, uint32_t *__restrict__ nitems)
+{
+    uint32_t ng = *ng_p;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        uint32_t og = order[g];
+        uint32_t sz = gbegin[og + 1] - gbegin[og];
+        nitems[g] = (sz + qpi - 1) / qpi;
+    }
+}
+
+__global__ void k_group_items(const uint32_t *__restrict__ gbegin, const uint32_t *__restrict__ order,
+                              const uint32_t *ng_p, int qpi, const uint32_t *__restrict__ ioff,
+                              uint2 *__restrict__ items)
+{
+    uint32_t ng = *ng_p;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        uint32_t og = order[g];
+        uint32_t b = gbegin[og], e = gbegin[og + 1];
+        uint32_t o = ioff[g];
+        for (uint32_t a = b; a < e; a += qpi) items[o++] = make_uint2(a, min((uint32_t)qpi, e - a));
+    }
+}
+
+// Next active list: active entries whose query was not certified.
+__global__ void k_compact(const uint32_t *__restrict__ active, const uint32_t *__restrict__ flags,
+                          const uint32_t *__restrict__ pos, int64_t m, uint32_t *__restrict__ out)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x)
+        if (flags[a]) out[pos[a]] = active ? active[a] : (uint32_t)a;
+}
+
+__global__ void k_iota(uint32_t *out, int64_t m)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x)
+        out[a] = (uint32_t)a;
+}
+
+}  // namespace knn

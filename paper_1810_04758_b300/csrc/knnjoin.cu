@@ -1,0 +1,708 @@
+// knnjoin.cu -- host orchestration and the C ABI (include/knnjoin.h).
+//
+// A join runs on one CUDA stream:
+//   a1 k_prep -> a2 k_eps_pairs, k_eps_hist x2, k_params x3 -> a3 k_keys ->
+//   a4 radix sort -> a5 k_gather -> pass loop { level cells + hash map,
+//   groups of the active queries, density order, work items, a7-a11 k_scan,
+//   compaction of the uncertified queries } until no query is left.
+// The pass loop is the device re-queue of Alg. 1 (failed queries go back to
+// the queue); each pass scans a ring of cells twice as wide as the last.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/knnjoin.h"
+#include "common.cuh"
+#include "grid.cuh"
+#include "primitives.cuh"
+#include "scan.cuh"
+
+using namespace knn;
+
+namespace {
+
+struct KnnError {
+    knnjoin_status st;
+    std::string msg;
+};
+
+[[noreturn]] void fail(knnjoin_status st, const std::string &msg) { throw KnnError{st, msg}; }
+
+void ck(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) fail(KNN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call) ck((call), #call)
+
+int grid_for(int64_t n, int threads, int nsm, int per_sm = 8)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)nsm * per_sm;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ---------------------------------------------------------------------------
+// Scratch memory: named device buffers that grow and are reused across joins.
+// ---------------------------------------------------------------------------
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free)(void *, void *) = nullptr;
+    void *user = nullptr;
+    void *get(size_t bytes)
+    {
+        void *p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, user);
+            if (!p) fail(KNN_ERR_NOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+            return p;
+        }
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            fail(KNN_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+        ck(e, "cudaMalloc");
+        return p;
+    }
+    void put(void *p)
+    {
+        if (!p) return;
+        if (free) free(p, user);
+        else cudaFree(p);
+    }
+};
+
+struct Scratch {
+    Allocator *al = nullptr;
+    struct Buf {
+        void *p = nullptr;
+        size_t cap = 0;
+    };
+    std::map<std::string, Buf> bufs;
+    template <class T>
+    T *get(const std::string &name, size_t count)
+    {
+        size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+        Buf &b = bufs[name];
+        if (b.cap < bytes) {
+            al->put(b.p);
+            b.p = nullptr;
+            b.cap = 0;
+            size_t nb = std::max(bytes, b.cap + b.cap / 4);
+            b.p = al->get(nb);
+            b.cap = nb;
+        }
+        return (T *)b.p;
+    }
+    void release()
+    {
+        for (auto &kv : bufs) al->put(kv.second.p);
+        bufs.clear();
+    }
+};
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// One join pipeline (stream + scratch + pinned readback).
+// ---------------------------------------------------------------------------
+struct Pipeline {
+    int device = 0;
+    int nsm = 148;
+    cudaStream_t s = nullptr;
+    Scratch sc;
+    uint32_t *pinned = nullptr;  // small host readback area
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    knnjoin_stats stats{};
+    float width_mult = 1.25f;
+
+    void init(int dev, cudaStream_t stream, Allocator *al)
+    {
+        device = dev;
+        s = stream;
+        sc.al = al;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaMallocHost(&pinned, 4096));
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+    }
+    void release()
+    {
+        sc.release();
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    template <class T>
+    T read1(const T *dev)
+    {
+        CK(cudaMemcpyAsync(pinned, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        T v;
+        memcpy(&v, pinned, sizeof(T));
+        return v;
+    }
+
+    // exclusive scan of m uint32 values (in may equal out)
+    void scan(const uint32_t *in, uint32_t *out, int64_t m, int depth = 0)
+    {
+        if (m <= 0) return;
+        int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
+        uint32_t *sums = sc.get<uint32_t>("scan_sums" + std::to_string(depth), (size_t)nb + 1);
+        k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, sums, m);
+        if (nb > 1) {
+            scan(sums, sums, nb, depth + 1);
+            k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, sums, m);
+        }
+    }
+
+    template <class K>
+    void radix_sort(K *&keys, uint32_t *&vals, K *&kalt, uint32_t *&valt, int64_t n, int bits)
+    {
+        if (n <= 1 || bits <= 0) return;
+        int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+        uint32_t *hist = sc.get<uint32_t>("rs_hist", (size_t)256 * nb);
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_rs_hist<K><<<nb, RS_THREADS, 0, s>>>(keys, n, shift, hist, nb);
+            scan(hist, hist, (int64_t)256 * nb);
+            k_rs_scatter<K><<<nb, RS_THREADS, 0, s>>>(keys, vals, kalt, valt, n, shift, hist, nb);
+            std::swap(keys, kalt);
+            std::swap(vals, valt);
+        }
+    }
+
+    void run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in);
+};
+
+__global__ void k_init_reduce(PrepReduce *r)
+{
+    int t = threadIdx.x;
+    if (t < MAX_DIM) {
+        r->lo_enc[t] = 0xffffffffu;
+        r->hi_enc[t] = 0u;
+    }
+    if (t == 0) {
+        r->min_lsb = 1 << 30;
+        r->max_msb = -(1 << 30);
+        r->nonfinite = 0;
+        r->eps_sum = 0.0;
+        r->eps_pairs = 0;
+    }
+    for (int i = t; i < 2 * 1024; i += blockDim.x) (&r->hist[0][0])[i] = 0;
+}
+
+size_t scan_smem_bytes(int d, int noff, int CH, int B)
+{
+    size_t s = (size_t)noff * 8 + (size_t)((noff + 1 + 3) & ~3) * 4 + (size_t)d * CH * 4 + (size_t)CH * 4;
+    s += (size_t)SCAN_WARPS * B * 4 * 2 + (size_t)SCAN_WARPS * 256 * 4;
+    s += (size_t)SCAN_WARPS * B * (8 + 4 + 4);
+    return s;
+}
+
+template <int DIM>
+void launch_scan(Pipeline &P, const ScanArgs &a, size_t smem)
+{
+    static bool configured[64] = {};
+    int dev = P.device;
+    if (!configured[dev & 63]) {
+        CK(cudaFuncSetAttribute(k_scan<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured[dev & 63] = true;
+    }
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<DIM>, SCAN_CTA, smem));
+    if (occ < 1) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM (K or d too large)");
+    unsigned grid = (unsigned)std::min<int64_t>(a.nitems, (int64_t)occ * P.nsm);
+    if (grid == 0) return;
+    k_scan<DIM><<<grid, SCAN_CTA, smem, P.s>>>(a);
+    CK(cudaGetLastError());
+}
+
+void dispatch_scan(Pipeline &P, int d, const ScanArgs &a, size_t smem)
+{
+    switch (d) {
+    case 1: launch_scan<1>(P, a, smem); break;
+    case 2: launch_scan<2>(P, a, smem); break;
+    case 3: launch_scan<3>(P, a, smem); break;
+    case 4: launch_scan<4>(P, a, smem); break;
+    case 5: launch_scan<5>(P, a, smem); break;
+    case 6: launch_scan<6>(P, a, smem); break;
+    case 7: launch_scan<7>(P, a, smem); break;
+    case 8: launch_scan<8>(P, a, smem); break;
+    default: fail(KNN_ERR_INVALID, "d out of range");
+    }
+}
+
+int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
+
+void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in)
+{
+    CK(cudaSetDevice(device));
+    const bool pts_dev = is_device_ptr(pts_in);
+    const bool ids_dev = is_device_ptr(ids_in);
+    const bool dist_dev = is_device_ptr(dist_in);
+    memset(&stats, 0, sizeof(stats));
+    stats.n = n;
+    stats.d = d;
+    stats.K = K;
+
+    const float *pts = pts_in;
+    if (!pts_dev) {
+        float *p = sc.get<float>("pts_in", (size_t)n * d);
+        CK(cudaMemcpyAsync(p, pts_in, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+        pts = p;
+    }
+    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)n * K);
+    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)n * K);
+    CK(cudaEventRecord(ev[0], s));
+
+    // a1
+    PrepReduce *red = sc.get<PrepReduce>("red", 1);
+    GridParams *gp = sc.get<GridParams>("gp", 1);
+    unsigned long long *st = sc.get<unsigned long long>("stats", 8);
+    CK(cudaMemsetAsync(st, 0, 8 * sizeof(unsigned long long), s));
+    k_init_reduce<<<1, 256, 0, s>>>(red);
+    float *xs = sc.get<float>("xs", (size_t)n * d);
+    k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red);
+    // a2
+    int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
+    smp = std::min(smp, n);
+    k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red);
+    ParamsIn pin;
+    pin.n = n;
+    pin.d = d;
+    pin.K = K;
+    pin.S = std::min<int64_t>(n, 256);
+    pin.m = std::min<int64_t>(n, 65536);
+    pin.width_mult = width_mult;
+    pin.start_level = 0;
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 0);
+    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 0);
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 1);
+    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 1);
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 2);
+    CK(cudaGetLastError());
+    GridParams hp = read1(gp);
+    if (hp.nonfinite) fail(KNN_ERR_INVALID, "points contain a NaN or infinite coordinate");
+    stats.eps_mean = hp.eps_mean;
+    stats.eps_min = hp.eps_min;
+    stats.cell_width = hp.w0;
+    stats.key_bits = hp.key_bits;
+    stats.fixed_point = hp.fixed_ok;
+    stats.start_level = hp.start_level;
+
+    // a3-a5
+    uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
+    uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
+    k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm);
+    radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
+    float *xsort = sc.get<float>("xsort", (size_t)n * d);
+    k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ev[1], s));
+
+    // pass loop
+    uint32_t *active = sc.get<uint32_t>("active", n), *active2 = sc.get<uint32_t>("active2", n);
+    uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
+    uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
+    uint32_t *small = sc.get<uint32_t>("small", 16);
+    k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n);
+    int64_t m = n;
+    int L = hp.start_level;
+    const int B = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
+    const int CH = d <= 6 ? 1024 : 512;
+    int noff = 1;
+    for (int k = 0; k < d; ++k) noff *= 3;
+    const size_t smem = scan_smem_bytes(d, noff, CH, B);
+    int pass = 0;
+    while (m > 0) {
+        if (L > hp.top_level) fail(KNN_ERR_CUDA, "internal: queries left uncertified at the top level");
+        const int shift = d * L;
+        // level cells over all points + hash map
+        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags);
+        scan(flags, rid, n);
+        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0);
+        uint32_t ncells = read1(small + 0);
+        uint32_t H = 1;
+        while (H < 2 * ncells) H <<= 1;
+        uint64_t *hkey = sc.get<uint64_t>("hkey", H);
+        uint2 *hval = sc.get<uint2>("hval", H);
+        CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
+        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1);
+        // groups of the active list
+        uint32_t *gbegin = sc.get<uint32_t>("gbegin", m + 1);
+        k_run_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(keys, active, m, shift, flags);
+        scan(flags, rid, m);
+        k_run_begin<<<grid_for(m, 256, nsm), 256, 0, s>>>(flags, rid, m, gbegin, small + 1);
+        CK(cudaMemsetAsync(small + 2, 0, 4, s));
+        uint32_t *skey = sc.get<uint32_t>("skey", m), *sval = sc.get<uint32_t>("sval", m);
+        uint32_t *skey2 = sc.get<uint32_t>("skey2", m), *sval2 = sc.get<uint32_t>("sval2", m);
+        k_group_sizes<<<grid_for(m, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2);
+        CK(cudaMemcpyAsync(pinned, small + 1, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint32_t ng = pinned[0], maxsz = pinned[1];
+        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2);
+        radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+        uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
+        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, nit);
+        scan(nit, ioff, ng);
+        CK(cudaMemcpyAsync(pinned, ioff + ng - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(pinned + 1, nit + ng - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint32_t nitems = pinned[0] + pinned[1];
+        uint2 *items = sc.get<uint2>("items", nitems);
+        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, ioff, items);
+        // scan
+        uint32_t *fail_f = sc.get<uint32_t>("fail", m);
+        CK(cudaMemsetAsync(small + 3, 0, 4, s));
+        ScanArgs a;
+        memset(&a, 0, sizeof(a));
+        a.xsort = xsort;
+        a.perm = perm;
+        a.keys = keys;
+        a.active = active;
+        a.items = items;
+        a.nitems = nitems;
+        a.counter = small + 3;
+        a.hkey = hkey;
+        a.hval = hval;
+        a.hmask = H - 1;
+        a.fail = fail_f;
+        a.out_ids = ids;
+        a.out_dist = dist;
+        a.stats = st;
+        a.n = n;
+        a.K = K;
+        a.level = L;
+        a.bits = hp.bits;
+        for (int k = 0; k < d; ++k) {
+            a.cmax0[k] = hp.cmax0[k];
+            a.lo[k] = hp.lo[k];
+        }
+        a.w0 = hp.w0;
+        a.fixed_ok = hp.fixed_ok;
+        a.F = hp.F;
+        a.B = B;
+        a.CH = CH;
+        a.noff = noff;
+        dispatch_scan(*this, d, a, smem);
+        // next active list
+        uint32_t *fpos = sc.get<uint32_t>("fpos", m);
+        scan(fail_f, fpos, m);
+        CK(cudaMemcpyAsync(pinned, fpos + m - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(pinned + 1, fail_f + m - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int64_t next = (int64_t)pinned[0] + pinned[1];
+        if (pass < 16) stats.pass_queries[pass] = m;
+        if (next > 0) k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, fail_f, fpos, m, active2);
+        std::swap(active, active2);
+        m = next;
+        ++L;
+        ++pass;
+    }
+    stats.passes = pass;
+    CK(cudaEventRecord(ev[2], s));
+    if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, s));
+    if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * n * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pinned, st, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    unsigned long long hs[4];
+    memcpy(hs, pinned, sizeof(hs));
+    stats.candidates = (int64_t)hs[0];
+    stats.overflow_queries = (int64_t)hs[1];
+    stats.band_entries = (int64_t)hs[2];
+    float ms = 0.f, ms1 = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[0], ev[2]));
+    CK(cudaEventElapsedTime(&ms1, ev[0], ev[1]));
+    stats.ms_total = ms;
+    stats.ms_index = ms1;
+}
+
+void validate(const float *points, int64_t n, int d, int K, const int32_t *ids, const double *dist)
+{
+    if (!points || !ids || !dist) fail(KNN_ERR_INVALID, "NULL pointer argument");
+    if (n < 2) fail(KNN_ERR_INVALID, "n must be >= 2");
+    if (n > 2147483647LL) fail(KNN_ERR_INVALID, "n must be <= 2^31 - 1");
+    if (d < 1 || d > MAX_DIM) fail(KNN_ERR_INVALID, "d must be in [1, 8]");
+    if (K < 1 || K > 256) fail(KNN_ERR_INVALID, "K must be in [1, 256]");
+    if ((int64_t)K > n - 1) fail(KNN_ERR_INVALID, "K must be <= n - 1");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context and serving queue
+// ---------------------------------------------------------------------------
+struct Job {
+    uint64_t id;
+    knnjoin_job job;
+    std::atomic<int> state{0};  // 0 queued, 1 running, 2 done, 3 cancelled
+    knnjoin_status status = KNN_OK;
+    std::string err;
+    knnjoin_stats stats{};
+};
+
+struct knnjoin_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr, serve_stream = nullptr;
+    bool own_stream = false;
+    Allocator al;
+    Pipeline main, serve;
+    std::string err;
+    knnjoin_config cfg{};
+    // serving
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
+    uint64_t next_id = 1;
+    std::thread worker;
+    bool stop = false;
+    bool worker_started = false;
+    int max_jobs = 64;
+};
+
+static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f);
+
+static void serve_loop(knnjoin_ctx *ctx)
+{
+    for (;;) {
+        std::shared_ptr<Job> j;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+            if (ctx->stop) return;
+            j = ctx->queue.front();
+            ctx->queue.pop_front();
+            int expect = 0;
+            if (!j->state.compare_exchange_strong(expect, 1)) continue;  // cancelled
+        }
+        knnjoin_status st = KNN_OK;
+        std::string msg;
+        try {
+            validate(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
+            ctx->serve.run(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
+        } catch (const KnnError &e) {
+            st = e.st;
+            msg = e.msg;
+        } catch (const std::exception &e) {
+            st = KNN_ERR_NOMEM;
+            msg = e.what();
+        }
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            j->status = st;
+            j->err = msg;
+            j->stats = ctx->serve.stats;
+            j->state.store(2);
+        }
+    }
+}
+
+static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f)
+{
+    try {
+        f();
+        if (ctx) ctx->err.clear();
+        return KNN_OK;
+    } catch (const KnnError &e) {
+        if (ctx) ctx->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->err = "host allocation failed";
+        return KNN_ERR_NOMEM;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->err = e.what();
+        return KNN_ERR_INVALID;
+    }
+}
+
+extern "C" {
+
+const char *knnjoin_version(void) { return "knnjoin-b300 0.1"; }
+
+knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
+{
+    if (!out) return KNN_ERR_INVALID;
+    *out = nullptr;
+    knnjoin_ctx *ctx = new (std::nothrow) knnjoin_ctx();
+    if (!ctx) return KNN_ERR_NOMEM;
+    knnjoin_status st = guard(ctx, [&] {
+        if (cfg) ctx->cfg = *cfg;
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        if (ctx->cfg.device < 0 || ctx->cfg.device >= ndev) fail(KNN_ERR_INVALID, "no such CUDA device");
+        ctx->device = ctx->cfg.device;
+        CK(cudaSetDevice(ctx->device));
+        if (ctx->cfg.stream) {
+            ctx->stream = (cudaStream_t)ctx->cfg.stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        CK(cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking));
+        ctx->al.alloc = ctx->cfg.alloc;
+        ctx->al.free = ctx->cfg.free;
+        ctx->al.user = ctx->cfg.user;
+        if ((ctx->al.alloc == nullptr) != (ctx->al.free == nullptr))
+            fail(KNN_ERR_INVALID, "alloc and free hooks must be given together");
+        ctx->main.init(ctx->device, ctx->stream, &ctx->al);
+        ctx->serve.init(ctx->device, ctx->serve_stream, &ctx->al);
+        if (ctx->cfg.width_mult > 0.0f) {
+            ctx->main.width_mult = ctx->cfg.width_mult;
+            ctx->serve.width_mult = ctx->cfg.width_mult;
+        }
+        if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
+    });
+    if (st != KNN_OK) {
+        knnjoin_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return KNN_OK;
+}
+
+void knnjoin_destroy(knnjoin_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->serve_stream) cudaStreamSynchronize(ctx->serve_stream);
+    ctx->main.release();
+    ctx->serve.release();
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
+    delete ctx;
+}
+
+knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                 int32_t *out_ids, double *out_dist)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        validate(points, n, d, K, out_ids, out_dist);
+        ctx->main.run(points, n, d, K, out_ids, out_dist);
+    });
+}
+
+knnjoin_status knnjoin_self_join_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs, int njobs)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (njobs < 0 || (njobs > 0 && !jobs)) fail(KNN_ERR_INVALID, "bad job list");
+        for (int i = 0; i < njobs; ++i)
+            validate(jobs[i].points, jobs[i].n, jobs[i].d, jobs[i].K, jobs[i].out_ids, jobs[i].out_dist);
+        for (int i = 0; i < njobs; ++i)
+            ctx->main.run(jobs[i].points, jobs[i].n, jobs[i].d, jobs[i].K, jobs[i].out_ids, jobs[i].out_dist);
+    });
+}
+
+knnjoin_status knnjoin_submit(knnjoin_ctx *ctx, const knnjoin_job *job, uint64_t *job_id)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!job || !job_id) fail(KNN_ERR_INVALID, "NULL job or job_id");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if ((int)ctx->queue.size() >= ctx->max_jobs) fail(KNN_ERR_QUEUE_FULL, "serving queue is full");
+        auto j = std::make_shared<Job>();
+        j->id = ctx->next_id++;
+        j->job = *job;
+        ctx->jobs[j->id] = j;
+        ctx->queue.push_back(j);
+        *job_id = j->id;
+        if (!ctx->worker_started) {
+            ctx->worker = std::thread(serve_loop, ctx);
+            ctx->worker_started = true;
+        }
+        ctx->cv.notify_one();
+    });
+}
+
+knnjoin_status knnjoin_poll(knnjoin_ctx *ctx, uint64_t job_id)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(job_id);
+    if (it == ctx->jobs.end()) {
+        ctx->err = "unknown job id";
+        return KNN_ERR_INVALID;
+    }
+    int stt = it->second->state.load();
+    if (stt == 0 || stt == 1) return KNN_ERR_NOT_READY;
+    knnjoin_status st = stt == 3 ? KNN_ERR_CANCELLED : it->second->status;
+    ctx->err = it->second->err;
+    ctx->jobs.erase(it);
+    return st;
+}
+
+knnjoin_status knnjoin_cancel(knnjoin_ctx *ctx, uint64_t job_id)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(job_id);
+    if (it == ctx->jobs.end()) {
+        ctx->err = "unknown job id";
+        return KNN_ERR_INVALID;
+    }
+    int expect = 0;
+    if (it->second->state.compare_exchange_strong(expect, 3)) return KNN_OK;
+    ctx->err = "job already started";
+    return KNN_ERR_INVALID;
+}
+
+knnjoin_status knnjoin_get_stats(knnjoin_ctx *ctx, uint64_t job_id, knnjoin_stats *out)
+{
+    if (!ctx || !out) return KNN_ERR_INVALID;
+    if (job_id == 0) {
+        *out = ctx->main.stats;
+        return KNN_OK;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(job_id);
+    if (it == ctx->jobs.end()) {
+        ctx->err = "unknown job id";
+        return KNN_ERR_INVALID;
+    }
+    *out = it->second->stats;
+    return KNN_OK;
+}
+
+const char *knnjoin_last_error(knnjoin_ctx *ctx)
+{
+    if (!ctx) return "NULL context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,14 @@
+/* Prints the sizes and field offsets of the ABI structs, so the Python
+ * binding's ctypes layouts can be checked against the C header. */
+#include <stddef.h>
+#include <stdio.h>
+#include "../../include/knnjoin.h"
+int main(void)
+{
+    printf("config %zu %zu %zu\n", sizeof(knnjoin_config), offsetof(knnjoin_config, width_mult),
+           offsetof(knnjoin_config, hbm_budget_bytes));
+    printf("job %zu %zu\n", sizeof(knnjoin_job), offsetof(knnjoin_job, out_dist));
+    printf("stats %zu %zu %zu\n", sizeof(knnjoin_stats), offsetof(knnjoin_stats, candidates),
+           offsetof(knnjoin_stats, ms_index));
+    return 0;
+}
