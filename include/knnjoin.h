@@ -98,6 +98,8 @@ typedef struct {
     int fixed_point;               /* 1 = integer fast path for exact distances */
     double ms_total;               /* device time of the join (events) */
     double ms_index;               /* device time up to the first pass */
+    double ms_scan;                /* device time of the scan kernel launches */
+    int64_t launches;              /* kernel launches of the join */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).

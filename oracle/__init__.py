@@ -77,6 +77,10 @@ def _load(mutant: str | None = None) -> ctypes.CDLL:
             lib.oracle_grid.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, P, P, P, ctypes.c_int]
             lib.oracle_grid.restype = ctypes.c_int
+            lib.oracle_grid_rows.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, P, ctypes.c_int64, P, P, P,
+                                             ctypes.c_int]
+            lib.oracle_grid_rows.restype = ctypes.c_int
             lib.oracle_select_epsilon.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                   P, ctypes.c_int]
             lib.oracle_select_epsilon.restype = ctypes.c_double
@@ -141,6 +145,22 @@ def grid(points: np.ndarray, K: int, width_mult: float = 1.0, threads: int = 0,
                  pass_queries=[int(st.pass_queries[i]) for i in range(min(st.passes, 64))],
                  pass_candidates=[int(st.pass_candidates[i]) for i in range(min(st.passes, 64))])
     return ids, dist, stats
+
+
+def grid_rows(points: np.ndarray, K: int, rows, width_mult: float = 1.0, threads: int = 0):
+    """Grid join of the query rows `rows` only: (ids, dist, stats), arrays [len(rows), K]."""
+    p = _prep(points)
+    n, d = p.shape
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    ids = np.empty((len(r), K), np.int32)
+    dist = np.empty((len(r), K), np.float64)
+    st = GridStats()
+    rc = _load().oracle_grid_rows(_ptr(p), n, d, K, width_mult, _ptr(r), len(r), _ptr(ids),
+                                  _ptr(dist), ctypes.byref(st), threads)
+    if rc:
+        raise ValueError("oracle_grid_rows: invalid arguments")
+    return ids, dist, dict(candidates=int(st.candidates), passes=int(st.passes),
+                           eps_min=st.eps_min, width=st.width)
 
 
 def select_epsilon(points: np.ndarray, K: int, threads: int = 0):

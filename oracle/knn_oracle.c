@@ -355,12 +355,18 @@ static void level_free(level_index *L)
     free(L->hslot);
 }
 
-/* Returns 0 on success, -1 on invalid arguments. */
-int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
-                int32_t *ids, double *dist, oracle_grid_stats *st, int nthreads)
+/* Grid join of the query rows `rows` (all rows when rows == NULL) against
+ * all of D; row r of ids/dist belongs to query rows[r] (or r).
+ * Returns 0 on success, -1 on invalid arguments. */
+int oracle_grid_rows(const float *pts, int64_t n, int d, int K, double width_mult,
+                     const int64_t *rows, int64_t nrows,
+                     int32_t *ids, double *dist, oracle_grid_stats *st, int nthreads)
 {
     if (!pts || !ids || !dist || n < 2 || d < 1 || d > 16 || K < 1 || K > n - 1)
         return -1;
+    if (rows)
+        for (int64_t r = 0; r < nrows; ++r)
+            if (rows[r] < 0 || rows[r] >= n) return -1;
     int nt = threads_or_default(nthreads);
     oracle_grid_stats local;
     if (!st) st = &local;
@@ -394,11 +400,13 @@ int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
         c0[i] = exact_floor_div(pts[i], w);
 
     int64_t *cl = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n * d));
-    int64_t *active = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    char *fail = (char *)malloc((size_t)n);
-    int64_t nactive = n;
-    for (int64_t i = 0; i < n; ++i) active[i] = i;
+    int64_t cap = (rows && nrows > n) ? nrows : n;
+    int64_t *active = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    char *fail = (char *)malloc((size_t)cap);
+    /* active entries are output rows; the query of row a is rows[a] (or a) */
+    int64_t nactive = rows ? nrows : n;
+    for (int64_t i = 0; i < nactive; ++i) active[i] = i;
 
     int64_t noffs = 1;
     for (int k = 0; k < d; ++k) noffs *= 3;
@@ -424,7 +432,8 @@ int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
             int64_t nb[16];
             #pragma omp for schedule(dynamic, 256)
             for (int64_t a = 0; a < nactive; ++a) {
-                int64_t i = active[a];
+                int64_t row = active[a];
+                int64_t i = rows ? rows[row] : row;
                 const float *q = pts + i * d;
                 const int64_t *cq = cl + i * d;
                 int cnt = 0;
@@ -475,7 +484,7 @@ int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
 #endif
                 }
                 fail[a] = (char)!ok;
-                if (ok) write_row(top, K, ids + i * K, dist + i * K);
+                if (ok) write_row(top, K, ids + row * K, dist + row * K);
             }
             free(top);
         }
@@ -494,6 +503,12 @@ int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
     }
     free(c0); free(cl); free(active); free(next); free(fail);
     return 0;
+}
+
+int oracle_grid(const float *pts, int64_t n, int d, int K, double width_mult,
+                int32_t *ids, double *dist, oracle_grid_stats *st, int nthreads)
+{
+    return oracle_grid_rows(pts, n, d, K, width_mult, NULL, 0, ids, dist, st, nthreads);
 }
 
 /* Size of the stats struct, so the Python side can check its layout. */

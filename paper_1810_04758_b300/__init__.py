@@ -55,7 +55,8 @@ class KnnjoinStats(ctypes.Structure):
                 ("eps_mean", ctypes.c_double), ("eps_min", ctypes.c_double),
                 ("cell_width", ctypes.c_double), ("key_bits", ctypes.c_int),
                 ("fixed_point", ctypes.c_int), ("ms_total", ctypes.c_double),
-                ("ms_index", ctypes.c_double)]
+                ("ms_index", ctypes.c_double), ("ms_scan", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}

@@ -140,6 +140,8 @@ struct Pipeline {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     knnjoin_stats stats{};
     float width_mult = 1.25f;
+    int64_t launches = 0;
+    cudaEvent_t evs[2] = {nullptr, nullptr};
 
     void init(int dev, cudaStream_t stream, Allocator *al)
     {
@@ -149,6 +151,7 @@ struct Pipeline {
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaMallocHost(&pinned, 4096));
         for (auto &e : ev) CK(cudaEventCreate(&e));
+        for (auto &e : evs) CK(cudaEventCreate(&e));
     }
     void release()
     {
@@ -156,6 +159,8 @@ struct Pipeline {
         if (pinned) cudaFreeHost(pinned);
         pinned = nullptr;
         for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : evs)
             if (e) cudaEventDestroy(e);
     }
 
@@ -175,10 +180,10 @@ struct Pipeline {
         if (m <= 0) return;
         int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
         uint32_t *sums = sc.get<uint32_t>("scan_sums" + std::to_string(depth), (size_t)nb + 1);
-        k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, sums, m);
+        k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, sums, m); ++launches;
         if (nb > 1) {
             scan(sums, sums, nb, depth + 1);
-            k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, sums, m);
+            k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, sums, m); ++launches;
         }
     }
 
@@ -189,9 +194,9 @@ struct Pipeline {
         int nb = (int)((n + RS_TILE - 1) / RS_TILE);
         uint32_t *hist = sc.get<uint32_t>("rs_hist", (size_t)256 * nb);
         for (int shift = 0; shift < bits; shift += 8) {
-            k_rs_hist<K><<<nb, RS_THREADS, 0, s>>>(keys, n, shift, hist, nb);
+            k_rs_hist<K><<<nb, RS_THREADS, 0, s>>>(keys, n, shift, hist, nb); ++launches;
             scan(hist, hist, (int64_t)256 * nb);
-            k_rs_scatter<K><<<nb, RS_THREADS, 0, s>>>(keys, vals, kalt, valt, n, shift, hist, nb);
+            k_rs_scatter<K><<<nb, RS_THREADS, 0, s>>>(keys, vals, kalt, valt, n, shift, hist, nb); ++launches;
             std::swap(keys, kalt);
             std::swap(vals, valt);
         }
@@ -240,6 +245,7 @@ void launch_scan(Pipeline &P, const ScanArgs &a, size_t smem)
     unsigned grid = (unsigned)std::min<int64_t>(a.nitems, (int64_t)occ * P.nsm);
     if (grid == 0) return;
     k_scan<DIM><<<grid, SCAN_CTA, smem, P.s>>>(a);
+    ++P.launches;
     CK(cudaGetLastError());
 }
 
@@ -267,6 +273,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const bool ids_dev = is_device_ptr(ids_in);
     const bool dist_dev = is_device_ptr(dist_in);
     memset(&stats, 0, sizeof(stats));
+    launches = 0;
+    double ms_scan = 0.0;
     stats.n = n;
     stats.d = d;
     stats.K = K;
@@ -286,13 +294,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     GridParams *gp = sc.get<GridParams>("gp", 1);
     unsigned long long *st = sc.get<unsigned long long>("stats", 8);
     CK(cudaMemsetAsync(st, 0, 8 * sizeof(unsigned long long), s));
-    k_init_reduce<<<1, 256, 0, s>>>(red);
+    k_init_reduce<<<1, 256, 0, s>>>(red); ++launches;
     float *xs = sc.get<float>("xs", (size_t)n * d);
-    k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red);
+    k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red); ++launches;
     // a2
     int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
     smp = std::min(smp, n);
-    k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red);
+    k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red); ++launches;
     ParamsIn pin;
     pin.n = n;
     pin.d = d;
@@ -301,11 +309,11 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     pin.m = std::min<int64_t>(n, 65536);
     pin.width_mult = width_mult;
     pin.start_level = 0;
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 0);
-    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 0);
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 1);
-    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 1);
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 2);
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
+    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 0); ++launches;
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
+    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 1); ++launches;
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
     CK(cudaGetLastError());
     GridParams hp = read1(gp);
     if (hp.nonfinite) fail(KNN_ERR_INVALID, "points contain a NaN or infinite coordinate");
@@ -319,10 +327,10 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // a3-a5
     uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
     uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
-    k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm);
+    k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
     radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
     float *xsort = sc.get<float>("xsort", (size_t)n * d);
-    k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort);
+    k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[1], s));
 
@@ -331,7 +339,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
     uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
     uint32_t *small = sc.get<uint32_t>("small", 16);
-    k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n);
+    k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n); ++launches;
     int64_t m = n;
     int L = hp.start_level;
     const int B = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
@@ -344,39 +352,39 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         if (L > hp.top_level) fail(KNN_ERR_CUDA, "internal: queries left uncertified at the top level");
         const int shift = d * L;
         // level cells over all points + hash map
-        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags);
+        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
         scan(flags, rid, n);
-        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0);
+        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
         uint32_t ncells = read1(small + 0);
         uint32_t H = 1;
         while (H < 2 * ncells) H <<= 1;
         uint64_t *hkey = sc.get<uint64_t>("hkey", H);
         uint2 *hval = sc.get<uint2>("hval", H);
         CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
-        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1);
+        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1); ++launches;
         // groups of the active list
         uint32_t *gbegin = sc.get<uint32_t>("gbegin", m + 1);
-        k_run_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(keys, active, m, shift, flags);
+        k_run_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(keys, active, m, shift, flags); ++launches;
         scan(flags, rid, m);
-        k_run_begin<<<grid_for(m, 256, nsm), 256, 0, s>>>(flags, rid, m, gbegin, small + 1);
+        k_run_begin<<<grid_for(m, 256, nsm), 256, 0, s>>>(flags, rid, m, gbegin, small + 1); ++launches;
         CK(cudaMemsetAsync(small + 2, 0, 4, s));
         uint32_t *skey = sc.get<uint32_t>("skey", m), *sval = sc.get<uint32_t>("sval", m);
         uint32_t *skey2 = sc.get<uint32_t>("skey2", m), *sval2 = sc.get<uint32_t>("sval2", m);
-        k_group_sizes<<<grid_for(m, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2);
+        k_group_sizes<<<grid_for(m, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
         CK(cudaMemcpyAsync(pinned, small + 1, 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         uint32_t ng = pinned[0], maxsz = pinned[1];
-        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2);
+        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
         radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
         uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
-        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, nit);
+        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, nit); ++launches;
         scan(nit, ioff, ng);
         CK(cudaMemcpyAsync(pinned, ioff + ng - 1, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(pinned + 1, nit + ng - 1, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         uint32_t nitems = pinned[0] + pinned[1];
         uint2 *items = sc.get<uint2>("items", nitems);
-        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, ioff, items);
+        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, ioff, items); ++launches;
         // scan
         uint32_t *fail_f = sc.get<uint32_t>("fail", m);
         CK(cudaMemsetAsync(small + 3, 0, 4, s));
@@ -410,7 +418,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.B = B;
         a.CH = CH;
         a.noff = noff;
+        CK(cudaEventRecord(evs[0], s));
         dispatch_scan(*this, d, a, smem);
+        CK(cudaEventRecord(evs[1], s));
         // next active list
         uint32_t *fpos = sc.get<uint32_t>("fpos", m);
         scan(fail_f, fpos, m);
@@ -418,8 +428,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         CK(cudaMemcpyAsync(pinned + 1, fail_f + m - 1, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         int64_t next = (int64_t)pinned[0] + pinned[1];
+        {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
+            ms_scan += t;
+        }
         if (pass < 16) stats.pass_queries[pass] = m;
-        if (next > 0) k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, fail_f, fpos, m, active2);
+        if (next > 0) k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, fail_f, fpos, m, active2); ++launches;
         std::swap(active, active2);
         m = next;
         ++L;
@@ -442,6 +457,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     CK(cudaEventElapsedTime(&ms1, ev[0], ev[1]));
     stats.ms_total = ms;
     stats.ms_index = ms1;
+    stats.ms_scan = ms_scan;
+    stats.launches = launches;
 }
 
 void validate(const float *points, int64_t n, int d, int K, const int32_t *ids, const double *dist)

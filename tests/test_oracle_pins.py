@@ -302,3 +302,12 @@ def test_pins_catch_planted_mistakes(mutant):
 
 def test_pins_pass_unmutated():
     assert not pins_fail(None)
+
+
+def test_grid_rows_matches_full_grid():
+    p = gen.make_points("expo", 20000, 3, seed=6)
+    ig, dg, _ = oracle.grid(p, 16)
+    rows = np.array([5, 19999, 0, 777, 777, 12345])
+    ir, dr, _ = oracle.grid_rows(p, 16, rows)
+    np.testing.assert_array_equal(ir, ig[rows])
+    np.testing.assert_array_equal(dr, dg[rows])
