@@ -144,6 +144,32 @@ knnjoin_status knnjoin_get_stats(knnjoin_ctx *ctx, uint64_t job_id, knnjoin_stat
  * next call on the context. */
 const char *knnjoin_last_error(knnjoin_ctx *ctx);
 
+/* Largest n accepted by knnjoin_self_join_noalloc. */
+#define KNN_NOALLOC_MAX_POINTS 65536
+
+/* The paper has no counterpart to this entry point: it is a variant of
+ * knnjoin_self_join for callers that must not allocate -- code running
+ * inside another framework's memory pool or under a hard memory cap, or an
+ * embedding that forbids cudaMalloc/cudaFree behind its back.  It allocates
+ * nothing: its scratch is one fixed 16 MiB device array inside the library
+ * (held by every GPU that loads the library until the process exits).
+ *   points   : float32 [n][d], DEVICE memory (host pointers are rejected)
+ *   n, d, K  : as knnjoin_self_join, and n <= KNN_NOALLOC_MAX_POINTS
+ *   out_ids  : int32 [n][K], device memory
+ *   out_dist : float64 [n][K], device memory
+ *   stream   : cudaStream_t to run on (NULL = the legacy default stream)
+ *   errbuf   : optional buffer of errlen bytes for the error message
+ * The results are identical to knnjoin_self_join's.  The call blocks until
+ * the join is done.  KNN_ERR_INVALID for sizes beyond the limits or host
+ * pointers.  All calls share the one array, which keeps the previous call's
+ * contents; calls that overlap on the GPU race, so the caller serialises
+ * them.  The first call on a device sets up that device (looks up the
+ * array's address, creates timing events): make it before any stream
+ * capture. */
+knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t n, int d, int K,
+                                         int32_t *out_ids, double *out_dist, void *stream,
+                                         char *errbuf, size_t errlen);
+
 /* Library version string. */
 const char *knnjoin_version(void);
 

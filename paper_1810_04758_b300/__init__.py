@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_NOMEM", 3: "KNN_E
 # Every symbol include/knnjoin.h declares.
 EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_self_join_batch",
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
-           "knnjoin_last_error", "knnjoin_version")
+           "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc")
+KNN_NOALLOC_MAX_POINTS = 65536
 
 
 class KnnjoinConfig(ctypes.Structure):
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_get_stats.restype = I
     lib.knnjoin_last_error.argtypes = [P]
     lib.knnjoin_last_error.restype = ctypes.c_char_p
+    lib.knnjoin_self_join_noalloc.argtypes = [P, I64, I, I, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.knnjoin_self_join_noalloc.restype = I
     lib.knnjoin_version.argtypes = []
     lib.knnjoin_version.restype = ctypes.c_char_p
     _lib = lib
@@ -163,6 +166,18 @@ def knnjoin_poll(ctx: int, job_id: int) -> int:
 
 def knnjoin_cancel(ctx: int, job_id: int) -> int:
     return load_library().knnjoin_cancel(ctx, job_id)
+
+
+def knnjoin_self_join_noalloc(points: int, n: int, d: int, K: int, out_ids: int, out_dist: int,
+                              stream: int = 0) -> int:
+    """The allocation-free variant (device pointers only, n <= 65,536); see
+    include/knnjoin.h.  Raises KnnJoinError with the library's message."""
+    buf = ctypes.create_string_buffer(512)
+    st = load_library().knnjoin_self_join_noalloc(points, n, d, K, out_ids, out_dist, stream,
+                                                  buf, len(buf))
+    if st != KNN_OK:
+        raise KnnJoinError(st, buf.value.decode())
+    return st
 
 
 def knnjoin_get_stats(ctx: int, job_id: int = 0) -> dict:

@@ -723,3 +723,152 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Self-join without any allocation by the library.
+//
+// For callers that cannot allocate device memory themselves or let a
+// library do it -- code running under another framework's memory pool or a
+// hard memory cap, or an embedding that owns every allocation and forbids
+// cudaMalloc/cudaFree behind its back.  The join's scratch (coordinates in
+// SoA and key order, keys, permutation, cell tables, hash map, work items)
+// lives in one fixed device array declared below; the caller passes device
+// input and output buffers and a stream.
+//
+// Limits: n <= KNN_NOALLOC_MAX_POINTS (65,536), d <= 8, K <= 256; the array
+// is NOALLOC_SCRATCH_BYTES (16 MiB) and every GPU that loads this library
+// keeps it until the process exits.  All calls share the array and it keeps
+// the previous call's contents (the join initialises everything it reads),
+// so calls that overlap on the GPU (other threads, other streams) race and
+// must be serialised by the caller.  The first call on a device does a
+// one-time set-up there (it looks up the array's device address and creates
+// the timing events); make that first call before any stream capture.
+// ---------------------------------------------------------------------------
+static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+    cudaEvent_t ev[5] = {};
+    int nsm = 0;
+};
+
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+
+struct Bump {
+    unsigned char *base;
+    size_t cap, off;
+};
+
+void *bump_alloc(size_t bytes, void *user)
+{
+    Bump *b = (Bump *)user;
+    size_t o = (b->off + 255) & ~(size_t)255;
+    if (o + bytes > b->cap) return nullptr;
+    b->off = o + bytes;
+    return b->base + o;
+}
+
+void bump_free(void *, void *) {}
+
+// Worst-case upper bound of the scratch one join of n points needs.
+size_t noalloc_bytes_needed(int64_t n, int d)
+{
+    size_t H = 1;
+    while (H < (size_t)(2 * n)) H <<= 1;
+    size_t b = 0;
+    b += 2 * (size_t)n * d * 4;              // xs, xsort
+    b += 2 * (size_t)n * 8 + 2 * (size_t)n * 4;  // keys, perm (+ alternates)
+    b += 16 * ((size_t)n + 1) * 4;           // active lists, flags, scans, groups, fail
+    b += (size_t)n * 8;                      // work items
+    b += H * 16;                             // hash map
+    b += 256 * (((size_t)n + RS_TILE - 1) / RS_TILE) * 4 + 64 * 1024;  // histograms, sums, small
+    b += sizeof(PrepReduce) + sizeof(GridParams) + 64 * 256;          // alignment slack
+    return b;
+}
+
+}  // namespace
+
+extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t n, int d, int K,
+                                                    int32_t *out_ids, double *out_dist, void *stream,
+                                                    char *errbuf, size_t errlen)
+{
+    std::string msg;
+    knnjoin_status st = KNN_OK;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    try {
+        validate(points, n, d, K, out_ids, out_dist);
+        if (n > KNN_NOALLOC_MAX_POINTS)
+            fail(KNN_ERR_INVALID, "n = " + std::to_string(n) + " exceeds the no-allocation limit of " +
+                                      std::to_string(KNN_NOALLOC_MAX_POINTS) + " points");
+        if (noalloc_bytes_needed(n, d) > NOALLOC_SCRATCH_BYTES)
+            fail(KNN_ERR_INVALID, "problem does not fit the fixed scratch array");
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            fail(KNN_ERR_INVALID, "points must be device memory (this entry point copies nothing)");
+        }
+        const int dev = at.device;
+        if (dev < 0 || dev >= 64) fail(KNN_ERR_INVALID, "device ordinal out of range");
+        if (!is_device_ptr(out_ids) || !is_device_ptr(out_dist))
+            fail(KNN_ERR_INVALID, "out_ids and out_dist must be device memory");
+        CK(cudaSetDevice(dev));
+        NoallocDevice &D = g_noalloc_dev[dev];
+        {
+            std::lock_guard<std::mutex> lk(g_noalloc_mu);
+            if (!D.ready) {
+                void *ptr = nullptr;
+                CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+                D.scratch = (unsigned char *)ptr;
+                for (auto &e : D.ev) CK(cudaEventCreate(&e));
+                CK(cudaDeviceGetAttribute(&D.nsm, cudaDevAttrMultiProcessorCount, dev));
+                D.ready = true;
+            }
+        }
+        Bump bump{D.scratch, NOALLOC_SCRATCH_BYTES, 0};
+        Allocator al;
+        al.alloc = bump_alloc;
+        al.free = bump_free;
+        al.user = &bump;
+        alignas(64) static thread_local uint32_t readback[1024];
+        Pipeline P;
+        P.device = dev;
+        P.nsm = D.nsm;
+        P.s = (cudaStream_t)stream;
+        P.sc.al = &al;
+        P.pinned = readback;
+        for (int i = 0; i < 3; ++i) P.ev[i] = D.ev[i];
+        P.evs[0] = D.ev[3];
+        P.evs[1] = D.ev[4];
+        // Reserve the buffers whose size varies between passes at their
+        // largest, so no buffer is carved twice.
+        size_t H = 1;
+        while (H < (size_t)(2 * n)) H <<= 1;
+        const char *per_point[] = {"gbegin", "skey", "sval", "skey2", "sval2", "nit", "ioff", "fail", "fpos"};
+        for (const char *nm : per_point) P.sc.get<uint32_t>(nm, (size_t)n + 1);
+        P.sc.get<uint2>("items", (size_t)n + 1);
+        P.sc.get<uint64_t>("hkey", H);
+        P.sc.get<uint2>("hval", H);
+        P.sc.get<uint32_t>("scan_sums0", (size_t)(n + SCAN_TILE - 1) / SCAN_TILE + 2);
+        P.sc.get<uint32_t>("scan_sums1", 4);
+        P.run(points, n, d, K, out_ids, out_dist);
+    } catch (const KnnError &e) {
+        st = e.st;
+        msg = e.msg;
+    } catch (const std::exception &e) {
+        st = KNN_ERR_INVALID;
+        msg = e.what();
+    }
+    if (prev_dev >= 0) cudaSetDevice(prev_dev);
+    if (errbuf && errlen) {
+        size_t k = std::min(errlen - 1, msg.size());
+        memcpy(errbuf, msg.data(), k);
+        errbuf[k] = 0;
+    }
+    return st;
+}
