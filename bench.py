@@ -227,6 +227,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     ctx = kj.Context(device=local_rank, stream=stream)
     names = WORKLOADS[args.workload]
+    if args.configs:
+        names = [nm for nm in names if nm in args.configs.split(",")]
     hosts = {nm: gen.config_points(nm) for nm in names}
     dpts = {nm: torch.from_numpy(p).to(dev) for nm, (p, K) in hosts.items()}
     outs = {nm: (torch.empty((len(p), K), dtype=torch.int32, device=dev),
@@ -387,6 +389,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--configs", default="",
+                    help="comma list restricting the workload's point sets (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

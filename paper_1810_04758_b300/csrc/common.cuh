@@ -10,6 +10,10 @@ namespace knn {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_DIM = 8;
 
+// Coordinates in key order are stored AoS, each point padded to 2, 4 or 8
+// floats (8, 16 or 32 bytes: one or two aligned vector loads per point).
+__host__ __device__ constexpr int pad_dim(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
+
 // Per-join parameters computed on the device (steps a1-a2) and read back.
 struct GridParams {
     int n, d, K;

@@ -252,7 +252,8 @@ __global__ void k_gather(const float *__restrict__ xs, int64_t n, int d, const u
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         uint32_t i = perm[s];
-        for (int k = 0; k < d; ++k) xsort[(int64_t)k * n + s] = xs[(int64_t)k * n + i];
+        const int P = pad_dim(d);
+        for (int k = 0; k < P; ++k) xsort[(int64_t)s * P + k] = k < d ? xs[(int64_t)k * n + i] : 0.0f;
     }
 }
 
@@ -383,6 +384,25 @@ __global__ void k_compact(const uint32_t *__restrict__ active, const uint32_t *_
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
          a += (int64_t)gridDim.x * blockDim.x)
         if (flags[a]) out[pos[a]] = active ? active[a] : (uint32_t)a;
+}
+
+// flags[a] = (status[list[a]] == value)
+__global__ void k_status_flags(const uint32_t *__restrict__ list, const uint32_t *__restrict__ status,
+                               int64_t m, uint32_t value, uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x)
+        flags[a] = status[list[a]] == value;
+}
+
+// a11: every output distance holds the bit pattern of its canonical squared
+// distance D; replace it by the correctly rounded sqrt(D) (exact.cuh).
+__global__ void k_sqrt_rows(double *__restrict__ dist, int64_t count)
+{
+    unsigned long long *u = (unsigned long long *)dist;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = sqrt_bits(u[i]);
 }
 
 __global__ void k_iota(uint32_t *out, int64_t m)

@@ -31,6 +31,7 @@
 #include "grid.cuh"
 #include "primitives.cuh"
 #include "scan.cuh"
+#include "scan2.cuh"
 
 using namespace knn;
 
@@ -266,6 +267,60 @@ void dispatch_scan(Pipeline &P, int d, const ScanArgs &a, size_t smem)
 
 int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 
+size_t scan2_smem_bytes(int d, int QM, int E)
+{
+    const int BS = 32 * E, P = pad_dim(d);
+    size_t w = (size_t)QM * BS * 8 + (size_t)QM * P * 4 + (size_t)QM * 8 + 256 * 4;
+    return (size_t)S2_WARPS * ((w + 15) & ~(size_t)15);
+}
+
+template <int DIM, int E>
+void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
+{
+    constexpr int QM = E <= 4 ? 16 : 8;
+    static bool configured[64] = {};
+    int dev = P.device;
+    if (!configured[dev & 63]) {
+        CK(cudaFuncSetAttribute(k_scan2<DIM, QM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured[dev & 63] = true;
+    }
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan2<DIM, QM, E>, S2_CTA, smem));
+    if (occ < 1) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
+    unsigned grid = (unsigned)std::min<int64_t>(((int64_t)a.nitems + S2_WARPS - 1) / S2_WARPS,
+                                                (int64_t)occ * P.nsm);
+    if (grid == 0) return;
+    k_scan2<DIM, QM, E><<<grid, S2_CTA, smem, P.s>>>(a);
+    ++P.launches;
+    CK(cudaGetLastError());
+}
+
+template <int DIM>
+void dispatch_scan2_e(Pipeline &P, int E, const ScanArgs &a, size_t smem)
+{
+    switch (E) {
+    case 2: launch_scan2<DIM, 2>(P, a, smem); break;
+    case 4: launch_scan2<DIM, 4>(P, a, smem); break;
+    case 8: launch_scan2<DIM, 8>(P, a, smem); break;
+    default: fail(KNN_ERR_INVALID, "internal: bad buffer size");
+    }
+}
+
+void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
+{
+    switch (d) {
+    case 1: dispatch_scan2_e<1>(P, E, a, smem); break;
+    case 2: dispatch_scan2_e<2>(P, E, a, smem); break;
+    case 3: dispatch_scan2_e<3>(P, E, a, smem); break;
+    case 4: dispatch_scan2_e<4>(P, E, a, smem); break;
+    case 5: dispatch_scan2_e<5>(P, E, a, smem); break;
+    case 6: dispatch_scan2_e<6>(P, E, a, smem); break;
+    case 7: dispatch_scan2_e<7>(P, E, a, smem); break;
+    case 8: dispatch_scan2_e<8>(P, E, a, smem); break;
+    default: fail(KNN_ERR_INVALID, "d out of range");
+    }
+}
+
 void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in)
 {
     CK(cudaSetDevice(device));
@@ -329,24 +384,73 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
     k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
     radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
-    float *xsort = sc.get<float>("xsort", (size_t)n * d);
+    float *xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
     k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[1], s));
 
     // pass loop
     uint32_t *active = sc.get<uint32_t>("active", n), *active2 = sc.get<uint32_t>("active2", n);
+    uint32_t *ovl = sc.get<uint32_t>("ovl", n);
     uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
     uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
     uint32_t *small = sc.get<uint32_t>("small", 16);
+    uint32_t *status = sc.get<uint32_t>("fail", n);  // per sorted position
     k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n); ++launches;
     int64_t m = n;
     int L = hp.start_level;
-    const int B = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
+    // general kernel (scan.cuh)
+    const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
     const int CH = d <= 6 ? 1024 : 512;
     int noff = 1;
     for (int k = 0; k < d; ++k) noff *= 3;
-    const size_t smem = scan_smem_bytes(d, noff, CH, B);
+    const size_t smem1 = scan_smem_bytes(d, noff, CH, B1);
+    // fast kernel (scan2.cuh)
+    const bool fast = K + 32 <= 256;
+    const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
+    const int QM = E2 <= 4 ? 16 : 8;
+    const size_t smem2 = scan2_smem_bytes(d, QM, E2);
+
+    // work items of a list of sorted positions at the current level
+    auto make_items = [&](const uint32_t *list, int64_t mm, int shift, int qpi, uint32_t &nitems) -> uint2 * {
+        uint32_t *gbegin = sc.get<uint32_t>("gbegin", mm + 1);
+        k_run_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(keys, list, mm, shift, flags); ++launches;
+        scan(flags, rid, mm);
+        k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
+        CK(cudaMemsetAsync(small + 2, 0, 4, s));
+        uint32_t *skey = sc.get<uint32_t>("skey", mm), *sval = sc.get<uint32_t>("sval", mm);
+        uint32_t *skey2 = sc.get<uint32_t>("skey2", mm), *sval2 = sc.get<uint32_t>("sval2", mm);
+        k_group_sizes<<<grid_for(mm, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
+        CK(cudaMemcpyAsync(pinned, small + 1, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint32_t ng = pinned[0], maxsz = pinned[1];
+        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
+        radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+        uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
+        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
+        scan(nit, ioff, ng);
+        CK(cudaMemcpyAsync(pinned, ioff + ng - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(pinned + 1, nit + ng - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        nitems = pinned[0] + pinned[1];
+        uint2 *items = sc.get<uint2>("items", nitems);
+        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, items); ++launches;
+        return items;
+    };
+    // entries of `list` whose status is `value`, in order, into `out`
+    auto select_list = [&](const uint32_t *list, int64_t mm, uint32_t value, uint32_t *out) -> int64_t {
+        k_status_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, status, mm, value, flags); ++launches;
+        scan(flags, rid, mm);
+        CK(cudaMemcpyAsync(pinned, rid + mm - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(pinned + 1, flags + mm - 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int64_t cntv = (int64_t)pinned[0] + pinned[1];
+        if (cntv > 0) {
+            k_compact<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, flags, rid, mm, out); ++launches;
+        }
+        return cntv;
+    };
+
     int pass = 0;
     while (m > 0) {
         if (L > hp.top_level) fail(KNN_ERR_CUDA, "internal: queries left uncertified at the top level");
@@ -362,45 +466,17 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         uint2 *hval = sc.get<uint2>("hval", H);
         CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
         k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1); ++launches;
-        // groups of the active list
-        uint32_t *gbegin = sc.get<uint32_t>("gbegin", m + 1);
-        k_run_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(keys, active, m, shift, flags); ++launches;
-        scan(flags, rid, m);
-        k_run_begin<<<grid_for(m, 256, nsm), 256, 0, s>>>(flags, rid, m, gbegin, small + 1); ++launches;
-        CK(cudaMemsetAsync(small + 2, 0, 4, s));
-        uint32_t *skey = sc.get<uint32_t>("skey", m), *sval = sc.get<uint32_t>("sval", m);
-        uint32_t *skey2 = sc.get<uint32_t>("skey2", m), *sval2 = sc.get<uint32_t>("sval2", m);
-        k_group_sizes<<<grid_for(m, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
-        CK(cudaMemcpyAsync(pinned, small + 1, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        uint32_t ng = pinned[0], maxsz = pinned[1];
-        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
-        radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
-        uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
-        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, nit); ++launches;
-        scan(nit, ioff, ng);
-        CK(cudaMemcpyAsync(pinned, ioff + ng - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(pinned + 1, nit + ng - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        uint32_t nitems = pinned[0] + pinned[1];
-        uint2 *items = sc.get<uint2>("items", nitems);
-        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, SCAN_WARPS, ioff, items); ++launches;
-        // scan
-        uint32_t *fail_f = sc.get<uint32_t>("fail", m);
-        CK(cudaMemsetAsync(small + 3, 0, 4, s));
+
         ScanArgs a;
         memset(&a, 0, sizeof(a));
         a.xsort = xsort;
         a.perm = perm;
         a.keys = keys;
-        a.active = active;
-        a.items = items;
-        a.nitems = nitems;
         a.counter = small + 3;
         a.hkey = hkey;
         a.hval = hval;
         a.hmask = H - 1;
-        a.fail = fail_f;
+        a.fail = status;
         a.out_ids = ids;
         a.out_dist = dist;
         a.stats = st;
@@ -415,32 +491,46 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.w0 = hp.w0;
         a.fixed_ok = hp.fixed_ok;
         a.F = hp.F;
-        a.B = B;
+        a.B = B1;
         a.CH = CH;
         a.noff = noff;
+
+        uint32_t nitems = 0;
+        a.items = make_items(active, m, shift, fast ? QM : SCAN_WARPS, nitems);
+        a.active = active;
+        a.nitems = nitems;
+        CK(cudaMemsetAsync(small + 3, 0, 4, s));
         CK(cudaEventRecord(evs[0], s));
-        dispatch_scan(*this, d, a, smem);
+        if (fast) dispatch_scan2(*this, d, E2, a, smem2);
+        else dispatch_scan(*this, d, a, smem1);
         CK(cudaEventRecord(evs[1], s));
-        // next active list
-        uint32_t *fpos = sc.get<uint32_t>("fpos", m);
-        scan(fail_f, fpos, m);
-        CK(cudaMemcpyAsync(pinned, fpos + m - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(pinned + 1, fail_f + m - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        int64_t next = (int64_t)pinned[0] + pinned[1];
         {
+            CK(cudaEventSynchronize(evs[1]));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
             ms_scan += t;
         }
+        if (fast) {
+            // queries whose buffer overflowed (massive ties): general kernel
+            int64_t mo = select_list(active, m, 2, ovl);
+            if (mo > 0) {
+                a.items = make_items(ovl, mo, shift, SCAN_WARPS, nitems);
+                a.active = ovl;
+                a.nitems = nitems;
+                CK(cudaMemsetAsync(small + 3, 0, 4, s));
+                dispatch_scan(*this, d, a, smem1);
+                stats.overflow_queries += mo;
+            }
+        }
+        int64_t next = select_list(active, m, 1, active2);
         if (pass < 16) stats.pass_queries[pass] = m;
-        if (next > 0) k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, fail_f, fpos, m, active2); ++launches;
         std::swap(active, active2);
         m = next;
         ++L;
         ++pass;
     }
     stats.passes = pass;
+    k_sqrt_rows<<<grid_for(n * K, 256, nsm, 16), 256, 0, s>>>(dist, n * K); ++launches;
     CK(cudaEventRecord(ev[2], s));
     if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, s));
     if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * n * K, cudaMemcpyDeviceToHost, s));
@@ -450,7 +540,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     unsigned long long hs[4];
     memcpy(hs, pinned, sizeof(hs));
     stats.candidates = (int64_t)hs[0];
-    stats.overflow_queries = (int64_t)hs[1];
+    stats.overflow_queries += (int64_t)hs[1];
     stats.band_entries = (int64_t)hs[2];
     float ms = 0.f, ms1 = 0.f;
     CK(cudaEventElapsedTime(&ms, ev[0], ev[2]));
@@ -559,6 +649,19 @@ static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f)
         return KNN_ERR_INVALID;
     }
 }
+
+#ifdef KNN_PHASE_TIMING
+// Diagnostics build only: read (and optionally clear) the phase counters.
+extern "C" int knnjoin_debug_phases(unsigned long long *out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, knn::g_phase, sizeof(unsigned long long) * 8) != cudaSuccess) return 1;
+    if (reset) {
+        unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (cudaMemcpyToSymbol(knn::g_phase, z, sizeof(z)) != cudaSuccess) return 1;
+    }
+    return 0;
+}
+#endif
 
 extern "C" {
 
@@ -781,7 +884,7 @@ size_t noalloc_bytes_needed(int64_t n, int d)
     size_t H = 1;
     while (H < (size_t)(2 * n)) H <<= 1;
     size_t b = 0;
-    b += 2 * (size_t)n * d * 4;              // xs, xsort
+    b += (size_t)n * d * 4 + (size_t)n * pad_dim(d) * 4;  // xs, xsort
     b += 2 * (size_t)n * 8 + 2 * (size_t)n * 4;  // keys, perm (+ alternates)
     b += 16 * ((size_t)n + 1) * 4;           // active lists, flags, scans, groups, fail
     b += (size_t)n * 8;                      // work items

@@ -22,7 +22,8 @@
 //       box covers every cell;
 //   a10 flags queries that are not certified (they go to the next level:
 //       a ring of cells twice as wide);
-//   a11 writes certified rows (original ids, sqrt(D) correctly rounded).
+//   a11 writes certified rows: original ids and the bit patterns of D (their
+//       correctly rounded square roots are taken by k_sqrt_rows).
 // A query whose band overflows its buffer (massive ties) is redone in an
 // exact round in which every candidate carries its exact (D, id) key.
 #pragma once
@@ -35,7 +36,7 @@ constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CTA = SCAN_WARPS * 32;
 
 struct ScanArgs {
-    const float *xsort;        // [d][n] coordinates in key order
+    const float *xsort;        // [n][pad(d)] coordinates in key order (pad = 2, 4 or 8)
     const uint32_t *perm;      // key order -> original id
     const uint64_t *keys;      // sorted Morton keys
     const uint32_t *active;    // active list (sorted positions)
@@ -45,7 +46,7 @@ struct ScanArgs {
     const uint64_t *hkey;      // level hash map
     const uint2 *hval;
     uint32_t hmask;
-    uint32_t *fail;            // [active] 1 = not certified
+    uint32_t *fail;            // [n] per sorted position: 0 certified, 1 not, 2 overflow
     int32_t *out_ids;          // [n][K]
     double *out_dist;          // [n][K]
     unsigned long long *stats; // [0] candidates, [1] overflow rounds, [2] band entries
@@ -145,7 +146,7 @@ __device__ __forceinline__ uint64_t exact_d2(const float *q, const int32_t *qi, 
 {
     float c[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) c[k] = a.xsort[(int64_t)k * a.n + s];
+    for (int k = 0; k < DIM; ++k) c[k] = a.xsort[(int64_t)s * pad_dim(DIM) + k];
     if (a.fixed_ok) {
         int32_t ci[DIM];
 #pragma unroll
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
         int32_t qi[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            q[k] = a.xsort[(int64_t)k * a.n + qs];
+            q[k] = a.xsort[(int64_t)qs * pad_dim(DIM) + k];
             qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
         }
 
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                     uint32_t s = nb_range[lo].x + (g - nb_cum[lo]);
                     cs[t] = s;
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) cx[k * CH + t] = a.xsort[(int64_t)k * a.n + s];
+                    for (int k = 0; k < DIM; ++k) cx[k * CH + t] = a.xsort[(int64_t)s * pad_dim(DIM) + k];
                 }
                 __syncthreads();
                 if (active_w && !ovf) {
@@ -454,10 +455,10 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 for (int u = 0; u < mine; ++u)
                     if (rr[u] < (uint32_t)K) {
                         a.out_ids[row + rr[u]] = (int32_t)rid[u];
-                        a.out_dist[row + rr[u]] = __longlong_as_double((long long)sqrt_bits(rd[u]));
+                        a.out_dist[row + rr[u]] = __longlong_as_double((long long)rd[u]);  // D; k_sqrt_rows converts
                     }
             }
-            if (lane == 0) a.fail[qa] = certified ? 0u : 1u;
+            if (lane == 0) a.fail[qs] = certified ? 0u : 1u;
             if (exact_round || true) need_exact = exact_round ? false : need_exact;
         }
         __syncthreads();
