@@ -269,14 +269,43 @@ int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 
 size_t scan2_smem_bytes(int d, int QM, int E)
 {
-    const int BS = 32 * E, P = pad_dim(d);
-    size_t w = (size_t)QM * BS * 8 + (size_t)QM * P * 4 + (size_t)QM * 8 + 256 * 4;
+    const int BS = 32 * E, QP = query_row_floats(d);
+    size_t w = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4;
     return (size_t)S2_WARPS * ((w + 15) & ~(size_t)15);
+}
+
+// Fill the nearest-first neighbour order (scan2.cuh) on the current device.
+void ensure_nb_order(int dev)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev & 63]) return;
+    std::vector<uint16_t> tab;
+    tab.reserve(NB_ORDER_TOTAL);
+    for (int d = 1; d <= MAX_DIM; ++d) {
+        int no = 1;
+        for (int k = 0; k < d; ++k) no *= 3;
+        std::vector<std::pair<int, int>> v;
+        for (int o = 0; o < no; ++o) {
+            int moves = 0, r = o;
+            for (int k = 0; k < d; ++k) {
+                moves += (r % 3) != 1;
+                r /= 3;
+            }
+            v.push_back({moves, o});
+        }
+        std::stable_sort(v.begin(), v.end());
+        for (auto &e : v) tab.push_back((uint16_t)e.second);
+    }
+    CK(cudaMemcpyToSymbol(c_nb_order, tab.data(), tab.size() * sizeof(uint16_t)));
+    done[dev & 63] = true;
 }
 
 template <int DIM, int E>
 void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
 {
+    ensure_nb_order(P.device);
     constexpr int QM = E <= 4 ? 16 : 8;
     static bool configured[64] = {};
     int dev = P.device;

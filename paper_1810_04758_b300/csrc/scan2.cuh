@@ -59,6 +59,16 @@ __device__ unsigned long long g_phase[8];
 #endif
 
 constexpr int S2_WARPS = 4;
+
+// Neighbour offsets of the 3^d box, nearest first: for each d the offset
+// codes (base-3 digits, digit 1 = no move) ordered by how many dimensions
+// move (0, then faces, edges, ...).  Filled once per device by the host.
+constexpr int NB_ORDER_TOTAL = 3 + 9 + 27 + 81 + 243 + 729 + 2187 + 6561;
+__constant__ uint16_t c_nb_order[NB_ORDER_TOTAL];
+__host__ __device__ constexpr int nb_order_offset(int d)
+{
+    return d <= 1 ? 0 : nb_order_offset(d - 1) + (d == 2 ? 3 : d == 3 ? 9 : d == 4 ? 27 : d == 5 ? 81 : d == 6 ? 243 : d == 7 ? 729 : 2187);
+}
 constexpr int S2_CTA = S2_WARPS * 32;
 
 template <int DIM>
@@ -238,6 +248,56 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&V)[E], int lane)
     }
 }
 
+// Row of a query in shared memory: coordinates, current threshold, sorted
+// position (as float bits), padded to a multiple of 4 floats (vector loads).
+__host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) & ~3; }
+
+template <int DIM>
+__device__ __forceinline__ void load_query_row(const float *qc, int i, float (&q)[DIM], float &thr, uint32_t &qs)
+{
+    constexpr int QP = query_row_floats(DIM);
+    float r[QP];
+    const float4 *row = (const float4 *)(qc + i * QP);
+#pragma unroll
+    for (int v = 0; v < QP / 4; ++v) {
+        const float4 t = row[v];
+        r[4 * v] = t.x;
+        r[4 * v + 1] = t.y;
+        r[4 * v + 2] = t.z;
+        r[4 * v + 3] = t.w;
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[k] = r[k];
+    thr = r[DIM];
+    qs = __float_as_uint(r[DIM + 1]);
+}
+
+// FP32 squared distance; for d >= 4 even and odd dimensions accumulate in two
+// chains (shorter latency).  Either way the value is within (d + 2) 2^-24
+// relative of the exact squared distance (plus underflow terms far below
+// 2^-120), which the band factor 2^-15 covers.
+template <int DIM>
+__device__ __forceinline__ float dist2_f32(const float (&q)[DIM], const float (&c)[DIM])
+{
+    if (DIM < 4) {
+        float d2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float df = q[k] - c[k];
+            d2 = fmaf(df, df, d2);
+        }
+        return d2;
+    }
+    float e = 0.0f, o = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float df = q[k] - c[k];
+        if (k & 1) o = fmaf(df, df, o);
+        else e = fmaf(df, df, e);
+    }
+    return e + o;
+}
+
 // Certificate radius of a query at level `level` in cell `cell` (rounded
 // down): distance to the nearest face of the 3^d box beyond which points exist.
 template <int DIM>
@@ -268,21 +328,22 @@ __device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, uint32_t
 }
 
 template <int DIM, int QM, int E>
-__global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
+__global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = pad_dim(DIM);
+    constexpr int QP = query_row_floats(DIM);
     constexpr int B = 32 * E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = a.K, NOFF = a.noff;
 
     // per-warp shared memory
     constexpr int BS = B;
-    const size_t wbytes = (size_t)QM * BS * 8 + (size_t)QM * P * 4 + (size_t)QM * 8 + 256 * 4;
+    const size_t wbytes = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4;
     unsigned char *wb = smem + warp * ((wbytes + 15) & ~(size_t)15);
     uint64_t *buf = (uint64_t *)wb;            // [QM][BS]  (d2_32 bits << 32 | sorted index)
-    float *qc = (float *)(buf + QM * BS);      // [QM][P]
-    int *cnt = (int *)(qc + QM * P);           // [QM]
+    float *qc = (float *)(buf + QM * BS);      // [QM][QP] coords, threshold, sorted position
+    int *cnt = (int *)(qc + QM * QP);          // [QM]
     uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
     uint32_t *hist = qsv + QM;                 // [256]
 
@@ -308,25 +369,25 @@ __global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
             load_point<DIM>(a.xsort, s, c);
             qsv[lane] = s;
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) qc[lane * P + k] = c[k];
+            for (int k = 0; k < DIM; ++k) qc[lane * QP + k] = c[k];
         }
         __syncwarp();
         int cell[DIM];
         morton_decode(a.keys[qsv[0]] >> shift, DIM, nbits, cell);
-        // per-query state in registers: lane i holds query i's threshold,
-        // buffer count and sorted position; every use broadcasts it with one
-        // shuffle and only lane i updates it (no barriers, compact loop)
-        float my_thr = -1.0f;
+        // query state: threshold and sorted position sit in the query's row
+        // (one broadcast vector load gives a pair everything it needs); the
+        // buffer count lives in lane i's register for query i
         int my_cnt = 0;
-        uint32_t my_qs = ~0u;
         if (lane < Q) {
             float q[DIM];
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) q[k] = qc[lane * P + k];
+            for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
             const float R = cert_radius<DIM>(q, cell, cmaxL, a);
-            my_thr = isinf(R) ? __int_as_float(0x7f800000) : __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-14f);
-            my_qs = qsv[lane];
+            qc[lane * QP + DIM] = isinf(R) ? __int_as_float(0x7f800000)
+                                           : __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-14f);
+            qc[lane * QP + DIM + 1] = __uint_as_float(qsv[lane]);
         }
+        __syncwarp();
 
         KNN_PT(0);
         // a7 + a8
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
             uint32_t rb = 0, re = 0;
             if (o < NOFF) {
                 int nb[DIM];
-                int r = o;
+                int r = c_nb_order[nb_order_offset(DIM) + o];
                 bool ok = true;
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
@@ -379,15 +440,12 @@ __global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
                 }
+#pragma unroll 2
                 for (int i = 0; i < Q; ++i) {
-                    float d2 = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) {
-                        float df = qc[i * P + k] - c[k];
-                        d2 = fmaf(df, df, d2);
-                    }
-                    const float ti = __shfl_sync(FULL, my_thr, i);
-                    const uint32_t qi_s = __shfl_sync(FULL, my_qs, i);
+                    float qv[DIM], ti;
+                    uint32_t qi_s;
+                    load_query_row<DIM>(qc, i, qv, ti, qi_s);
+                    const float d2 = dist2_f32<DIM>(qv, c);
                     bool acc = valid && d2 <= ti && s != qi_s;
                     uint32_t bal = __ballot_sync(FULL, acc);
                     if (bal) {
@@ -409,7 +467,8 @@ __global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
                                 acc = false;
                                 nnew = 0;
                             }
-                            if (lane == i) my_thr = tnew;
+                            if (lane == 0) qc[i * QP + DIM] = tnew;
+                            __syncwarp();
                         }
                         if (acc) bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
                         if (lane == i) my_cnt = c0 < 0 ? -1 : c0 + nnew;
@@ -459,7 +518,7 @@ __global__ void __launch_bounds__(S2_CTA) k_scan2(ScanArgs a)
                 int32_t qi[DIM];
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
-                    q[k] = qc[i * P + k];
+                    q[k] = qc[i * QP + k];
                     qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
                 }
                 uint64_t D[E];
