@@ -151,7 +151,7 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx);
  * knnjoin_self_join for callers that must not allocate -- code running
  * inside another framework's memory pool or under a hard memory cap, or an
  * embedding that forbids cudaMalloc/cudaFree behind its back.  It allocates
- * nothing: its scratch is one fixed 16 MiB device array inside the library
+ * nothing: its scratch is one fixed 32 MiB device array inside the library
  * (held by every GPU that loads the library until the process exits).
  *   points   : float32 [n][d], DEVICE memory (host pointers are rejected)
  *   n, d, K  : as knnjoin_self_join, and n <= KNN_NOALLOC_MAX_POINTS
@@ -161,7 +161,9 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx);
  *   errbuf   : optional buffer of errlen bytes for the error message
  * The results are identical to knnjoin_self_join's.  The call blocks until
  * the join is done.  KNN_ERR_INVALID for sizes beyond the limits or host
- * pointers.  All calls share the one array, which keeps the previous call's
+ * pointers; KNN_ERR_NOMEM if an unusually spread-out input needs the cell
+ * tables of more grid levels than the array holds.  All calls share the one
+ * array, which keeps the previous call's
  * contents; calls that overlap on the GPU race, so the caller serialises
  * them.  The first call on a device sets up that device (looks up the
  * array's address, creates timing events): make it before any stream

@@ -9,6 +9,7 @@ namespace knn {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_DIM = 8;
+constexpr int MAX_LEVELS = 26;  // grid levels 0 .. 25 (at most 24 key bits per dimension)
 
 // Coordinates in key order are stored AoS, each point padded to 2, 4 or 8
 // floats (8, 16 or 32 bytes: one or two aligned vector loads per point).
@@ -27,6 +28,7 @@ struct GridParams {
     int key_bits;                    // d * bits
     int top_level;                   // level at which the grid is one cell
     int start_level;                 // level of the first pass
+    int finer;                       // levels below the search-distance width
     int nonfinite;                   // input holds NaN / Inf
 };
 
@@ -39,6 +41,7 @@ struct PrepReduce {
     double eps_sum;
     unsigned long long eps_pairs;
     unsigned hist[2][1024];
+    unsigned scount[256];            // sampled points' neighbours within eps_min
 };
 
 // Order-preserving float <-> uint32 encodings (for atomicMin/Max on floats).

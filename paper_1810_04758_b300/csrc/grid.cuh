@@ -148,11 +148,35 @@ struct ParamsIn {
     int64_t S, m;        // histogram samples / subset size
     float width_mult;    // cell side = width_mult * eps_min
     int start_level;
+    int max_finer;       // cap on levels finer than the search-distance width
 };
 
+// Density skew: neighbours of each sampled point among the subset within
+// the radius where about K are expected (eps_min scaled by (n/m)^(1/d)).
+__global__ void k_eps_count(const float *xs, int64_t n, int d, int64_t S, int64_t m,
+                            const GridParams *gp, PrepReduce *red)
+{
+    // radius at which a sample expects about K neighbours within the subset
+    const float e = gp->eps_min * powf((float)n / (float)m, 1.0f / (float)d);
+    if (!(e > 0.0f) || !isfinite(e)) return;
+    int64_t sstride = n / S, mstride = n / m;
+    for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+        unsigned c = 0;
+        int64_t si = s * sstride;
+        for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+            int64_t mj = t * mstride;
+            if (mj != si && dist_f32(xs, n, d, si, mj) < e) ++c;
+        }
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&red->scount[s], c);
+    }
+}
+
+__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in);
+
 // stage 0: eps_mean and the grid-independent fields; stage 1: eps_min
-// estimate from hist[0]; stage 2: refined eps_min from hist[1], cell side,
-// grid and key bits.
+// estimate from hist[0]; stage 2: refined eps_min from hist[1]; stage 3:
+// density skew, cell side, grid and key bits.
 __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int stage)
 {
     if (threadIdx.x || blockIdx.x) return;
@@ -178,6 +202,10 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
         gp->eps_min = 0.0f;
         return;
     }
+    if (stage == 3) {
+        k_params_grid(red, gp, in);
+        return;
+    }
     // cumulative count per sampled point reaches K (scaled to the subset)
     const unsigned *h = red->hist[stage - 1];
     float range = stage == 1 ? gp->eps_mean : 2.0f * gp->eps_min;
@@ -198,7 +226,12 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
     }
     if (!(range > 0.0f)) eps = gp->eps_mean;
     gp->eps_min = eps;
+}
 
+__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in)
+{
+    const int d = in.d;
+    const float eps = gp->eps_min;
     // cell side and grid
     float ext = 0.0f, mag = 0.0f;
     for (int k = 0; k < d; ++k) {
@@ -206,8 +239,24 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
         mag = fmaxf(mag, fmaxf(fabsf(gp->lo[k]), fabsf(gp->hi[k])));
     }
     int bmax = min(24, 63 / d);
+    // levels finer than the search-distance width, from the density skew of
+    // the sampled points: the densest sample over the mean, per dimension
+    double csum = 0.0;
+    unsigned cmaxs = 0;
+    for (int s = 0; s < (int)in.S && s < 256; ++s) {
+        csum += red->scount[s];
+        cmaxs = max(cmaxs, red->scount[s]);
+    }
+    int finer = 0;
+    if (csum > 0.0) {
+        double ratio = (double)cmaxs * (double)min((int64_t)256, in.S) / csum;
+        finer = (int)floor(log2(fmax(ratio, 1.0)) / d + 0.5);
+        finer = max(0, min(finer, in.max_finer));
+    }
+    gp->finer = finer;
     float w = in.width_mult * eps;
     if (!(w > 0.0f) || !isfinite(w)) w = ext > 0.0f ? ext : 1.0f;
+    w = ldexpf(w, -finer);
     float wf1 = ldexpf(mag, -21);                            // faces strictly increasing
     float wf2 = ext / (float)((1 << bmax) - 4);              // grid fits the key bits
     w = fmaxf(w, fmaxf(wf1, wf2));
@@ -226,6 +275,116 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
     gp->key_bits = bits * d;
     gp->top_level = bits;
     gp->start_level = min(in.start_level, bits);
+}
+
+// ---------------------------------------------------------------------------
+// Start level of every query (density adaptivity).  L(p) = the smallest level
+// at which the cell of sorted point p holds at least H points; equivalently
+// the minimum, over the windows of H consecutive sorted points that contain
+// p, of the level at which the window's first and last keys share a prefix
+// (a level-l cell is a run of equal key >> d*l).  Sliding-window minimum by
+// the van Herk / Gil-Werman method: per block of H windows a prefix and a
+// suffix minimum.  The query starts one level below: lvl[p] = max(0, L - 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t window_level(const uint64_t *keys, int64_t a, int64_t H, int d)
+{
+    uint64_t x = keys[a] ^ keys[a + H - 1];
+    int nb = x ? 64 - __clzll((long long)x) : 0;
+    return (uint32_t)((nb + d - 1) / d);
+}
+
+__global__ void k_window_blocks(const uint64_t *__restrict__ keys, int64_t nw, int64_t H, int d,
+                                uint8_t *__restrict__ pm, uint8_t *__restrict__ sm)
+{
+    const int64_t nblk = (nw + H - 1) / H;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = b * H, hi = min(nw, lo + H);
+        uint32_t m = 255;
+        for (int64_t a = lo; a < hi; ++a) {
+            m = min(m, window_level(keys, a, H, d));
+            pm[a] = (uint8_t)m;
+        }
+        m = 255;
+        for (int64_t a = hi - 1; a >= lo; --a) {
+            m = min(m, window_level(keys, a, H, d));
+            sm[a] = (uint8_t)m;
+        }
+    }
+}
+
+__global__ void k_start_levels(const uint8_t *__restrict__ pm, const uint8_t *__restrict__ sm, int64_t n,
+                               int64_t H, uint32_t top, uint32_t base, uint32_t *__restrict__ lvl)
+{
+    const int64_t nw = n - H + 1;  // number of windows (> 0 here)
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = max((int64_t)0, p - H + 1), hi = min(p, nw - 1);
+        uint32_t L;
+        if (lo / H == hi / H) L = (lo % H == 0) ? pm[hi] : sm[lo];
+        else L = min((uint32_t)sm[lo], (uint32_t)pm[hi]);
+        uint32_t l = L > 0 ? L - 1 : 0;
+        l = max(l, base);
+        lvl[p] = min(l, top);
+    }
+}
+
+__global__ void k_fill_u32(uint32_t *out, int64_t m, uint32_t v)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x)
+        out[a] = v;
+}
+
+// Sort keys (the level) of the active list, and the level range present.
+__global__ void k_level_keys(const uint32_t *__restrict__ list, const uint32_t *__restrict__ lvl, int64_t m,
+                             uint32_t *__restrict__ key, uint32_t *range)
+{
+    uint32_t lmin = 0xffffffffu, lmax = 0;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = lvl[list[a]];
+        key[a] = l;
+        lmin = min(lmin, l);
+        lmax = max(lmax, l);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lmin = min(lmin, __shfl_xor_sync(FULL, lmin, o));
+        lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&range[0], lmin);
+        atomicMax(&range[1], lmax);
+    }
+}
+
+// Group boundaries of a level-sorted list: a new group where the level or
+// the cell at that level changes.
+__global__ void k_run_flags_lv(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ list,
+                               const uint32_t *__restrict__ lvl, int64_t m, int d,
+                               uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = list[a], l = lvl[s];
+        uint32_t f = 1;
+        if (a > 0) {
+            const uint32_t s0 = list[a - 1], l0 = lvl[s0];
+            f = (l != l0) || ((keys[s] >> (d * l)) != (keys[s0] >> (d * l0)));
+        }
+        flags[a] = f;
+    }
+}
+
+// Uncertified queries move one level up (a ring of cells twice as wide).
+__global__ void k_bump_levels(const uint32_t *__restrict__ list, const uint32_t *__restrict__ status, int64_t m,
+                              uint32_t *__restrict__ lvl, uint32_t top)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = list[a];
+        if (status[s] == 1) lvl[s] = min(lvl[s] + 1, top);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -364,8 +523,10 @@ __global__ void k_group_nitems(const uint32_t *__restrict__ gbegin, const uint32
     }
 }
 
+// Item = (first list index, count | level << 16).
 __global__ void k_group_items(const uint32_t *__restrict__ gbegin, const uint32_t *__restrict__ order,
                               const uint32_t *ng_p, int qpi, const uint32_t *__restrict__ ioff,
+                              const uint32_t *__restrict__ list, const uint32_t *__restrict__ lvl,
                               uint2 *__restrict__ items)
 {
     uint32_t ng = *ng_p;
@@ -373,7 +534,8 @@ __global__ void k_group_items(const uint32_t *__restrict__ gbegin, const uint32_
         uint32_t og = order[g];
         uint32_t b = gbegin[og], e = gbegin[og + 1];
         uint32_t o = ioff[g];
-        for (uint32_t a = b; a < e; a += qpi) items[o++] = make_uint2(a, min((uint32_t)qpi, e - a));
+        uint32_t l = lvl[list[b]];
+        for (uint32_t a = b; a < e; a += qpi) items[o++] = make_uint2(a, min((uint32_t)qpi, e - a) | (l << 16));
     }
 }
 

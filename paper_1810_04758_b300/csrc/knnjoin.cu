@@ -221,6 +221,7 @@ __global__ void k_init_reduce(PrepReduce *r)
         r->eps_pairs = 0;
     }
     for (int i = t; i < 2 * 1024; i += blockDim.x) (&r->hist[0][0])[i] = 0;
+    for (int i = t; i < 256; i += blockDim.x) r->scount[i] = 0;
 }
 
 size_t scan_smem_bytes(int d, int noff, int CH, int B)
@@ -393,11 +394,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     pin.m = std::min<int64_t>(n, 65536);
     pin.width_mult = width_mult;
     pin.start_level = 0;
+    pin.max_finer = 3;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
     k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 0); ++launches;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
     k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 1); ++launches;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
+    k_eps_count<<<(unsigned)pin.S, 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red); ++launches;
+    k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
     CK(cudaGetLastError());
     GridParams hp = read1(gp);
     if (hp.nonfinite) fail(KNN_ERR_INVALID, "points contain a NaN or infinite coordinate");
@@ -418,6 +422,28 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[1], s));
 
+    // start level of every query (sliding-window cell counts)
+    uint32_t *lvl = sc.get<uint32_t>("lvl", n);
+    {
+        // target count of a query's parent cell: between the expected counts
+        // of the ideal level's parent and of the ideal level itself
+        const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
+        const double ideal = std::pow(2.0 * (double)width_mult, d) * (double)K / Vd;
+        int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
+        if (hp.finer == 0) {
+            // no density skew: every query starts at the search-distance width
+            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.start_level); ++launches;
+        } else if (n >= H && hp.top_level > 0) {
+            const int64_t nw = n - H + 1;
+            uint8_t *pm = sc.get<uint8_t>("win_pm", nw), *smn = sc.get<uint8_t>("win_sm", nw);
+            const int64_t nblk = (nw + H - 1) / H;
+            k_window_blocks<<<grid_for(nblk, 128, nsm, 16), 128, 0, s>>>(keys, nw, H, d, pm, smn); ++launches;
+            k_start_levels<<<grid_for(n, 256, nsm), 256, 0, s>>>(pm, smn, n, H, hp.top_level, hp.start_level, lvl); ++launches;
+        } else {
+            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.top_level); ++launches;
+        }
+    }
+
     // pass loop
     uint32_t *active = sc.get<uint32_t>("active", n), *active2 = sc.get<uint32_t>("active2", n);
     uint32_t *ovl = sc.get<uint32_t>("ovl", n);
@@ -425,9 +451,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
     uint32_t *small = sc.get<uint32_t>("small", 16);
     uint32_t *status = sc.get<uint32_t>("fail", n);  // per sorted position
+    uint32_t *lkey = sc.get<uint32_t>("lkey", n), *lkey2 = sc.get<uint32_t>("lkey2", n);
     k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n); ++launches;
     int64_t m = n;
-    int L = hp.start_level;
     // general kernel (scan.cuh)
     const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
     const int CH = d <= 6 ? 1024 : 512;
@@ -440,10 +466,34 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const int QM = E2 <= 4 ? 16 : 8;
     const size_t smem2 = scan2_smem_bytes(d, QM, E2);
 
-    // work items of a list of sorted positions at the current level
-    auto make_items = [&](const uint32_t *list, int64_t mm, int shift, int qpi, uint32_t &nitems) -> uint2 * {
+    // per-level cell hash maps, built on first use
+    struct LevelTab {
+        uint64_t *hkey = nullptr;
+        uint2 *hval = nullptr;
+        uint32_t mask = 0;
+        bool built = false;
+    };
+    LevelTab tabs[MAX_LEVELS];
+    auto build_level = [&](int L) {
+        if (tabs[L].built) return;
+        const int shift = d * L;
+        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
+        scan(flags, rid, n);
+        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
+        uint32_t ncells = read1(small + 0);
+        uint32_t H = 1;
+        while (H < 2 * ncells) H <<= 1;
+        uint64_t *hkey = sc.get<uint64_t>("hkey" + std::to_string(L), H);
+        uint2 *hval = sc.get<uint2>("hval" + std::to_string(L), H);
+        CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
+        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1); ++launches;
+        tabs[L] = {hkey, hval, H - 1, true};
+    };
+
+    // work items of a (level, position)-ordered list of sorted positions
+    auto make_items = [&](const uint32_t *list, int64_t mm, int qpi, uint32_t &nitems) -> uint2 * {
         uint32_t *gbegin = sc.get<uint32_t>("gbegin", mm + 1);
-        k_run_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(keys, list, mm, shift, flags); ++launches;
+        k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(keys, list, lvl, mm, d, flags); ++launches;
         scan(flags, rid, mm);
         k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
         CK(cudaMemsetAsync(small + 2, 0, 4, s));
@@ -463,7 +513,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         CK(cudaStreamSynchronize(s));
         nitems = pinned[0] + pinned[1];
         uint2 *items = sc.get<uint2>("items", nitems);
-        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, items); ++launches;
+        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, list, lvl, items); ++launches;
         return items;
     };
     // entries of `list` whose status is `value`, in order, into `out`
@@ -481,20 +531,24 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     };
 
     int pass = 0;
+    int first_level = -1;
     while (m > 0) {
-        if (L > hp.top_level) fail(KNN_ERR_CUDA, "internal: queries left uncertified at the top level");
-        const int shift = d * L;
-        // level cells over all points + hash map
-        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
-        scan(flags, rid, n);
-        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
-        uint32_t ncells = read1(small + 0);
-        uint32_t H = 1;
-        while (H < 2 * ncells) H <<= 1;
-        uint64_t *hkey = sc.get<uint64_t>("hkey", H);
-        uint2 *hval = sc.get<uint2>("hval", H);
-        CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
-        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1); ++launches;
+        if (pass > 4 * MAX_LEVELS) fail(KNN_ERR_CUDA, "internal: too many passes");
+        // order the active list by level (stable: positions stay ordered
+        // within a level) and build the levels' hash maps
+        k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
+        k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
+        k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
+        CK(cudaMemcpyAsync(pinned, small + 4, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const uint32_t lmin = pinned[0], lmax = pinned[1];
+        if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
+        if (first_level < 0) first_level = (int)lmin;
+        if (lmin != lmax) {
+            uint32_t *kk = lkey, *kk2 = lkey2;
+            radix_sort<uint32_t>(kk, active, kk2, active2, m, bitlen32(lmax));
+        }
+        for (uint32_t L = lmin; L <= lmax; ++L) build_level((int)L);
 
         ScanArgs a;
         memset(&a, 0, sizeof(a));
@@ -502,16 +556,17 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.perm = perm;
         a.keys = keys;
         a.counter = small + 3;
-        a.hkey = hkey;
-        a.hval = hval;
-        a.hmask = H - 1;
+        for (int L = 0; L < MAX_LEVELS; ++L) {
+            a.hkeyL[L] = tabs[L].hkey;
+            a.hvalL[L] = tabs[L].hval;
+            a.hmaskL[L] = tabs[L].mask;
+        }
         a.fail = status;
         a.out_ids = ids;
         a.out_dist = dist;
         a.stats = st;
         a.n = n;
         a.K = K;
-        a.level = L;
         a.bits = hp.bits;
         for (int k = 0; k < d; ++k) {
             a.cmax0[k] = hp.cmax0[k];
@@ -525,7 +580,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.noff = noff;
 
         uint32_t nitems = 0;
-        a.items = make_items(active, m, shift, fast ? QM : SCAN_WARPS, nitems);
+        a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
         a.active = active;
         a.nitems = nitems;
         CK(cudaMemsetAsync(small + 3, 0, 4, s));
@@ -543,7 +598,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             // queries whose buffer overflowed (massive ties): general kernel
             int64_t mo = select_list(active, m, 2, ovl);
             if (mo > 0) {
-                a.items = make_items(ovl, mo, shift, SCAN_WARPS, nitems);
+                a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
                 a.active = ovl;
                 a.nitems = nitems;
                 CK(cudaMemsetAsync(small + 3, 0, 4, s));
@@ -551,13 +606,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 stats.overflow_queries += mo;
             }
         }
+        k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
         int64_t next = select_list(active, m, 1, active2);
         if (pass < 16) stats.pass_queries[pass] = m;
         std::swap(active, active2);
         m = next;
-        ++L;
         ++pass;
     }
+    stats.start_level = first_level;
     stats.passes = pass;
     k_sqrt_rows<<<grid_for(n * K, 256, nsm, 16), 256, 0, s>>>(dist, n * K); ++launches;
     CK(cudaEventRecord(ev[2], s));
@@ -868,7 +924,7 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx)
 // input and output buffers and a stream.
 //
 // Limits: n <= KNN_NOALLOC_MAX_POINTS (65,536), d <= 8, K <= 256; the array
-// is NOALLOC_SCRATCH_BYTES (16 MiB) and every GPU that loads this library
+// is NOALLOC_SCRATCH_BYTES (32 MiB) and every GPU that loads this library
 // keeps it until the process exits.  All calls share the array and it keeps
 // the previous call's contents (the join initialises everything it reads),
 // so calls that overlap on the GPU (other threads, other streams) race and
@@ -876,7 +932,7 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx)
 // one-time set-up there (it looks up the array's device address and creates
 // the timing events); make that first call before any stream capture.
 // ---------------------------------------------------------------------------
-static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
+static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)32 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -917,7 +973,8 @@ size_t noalloc_bytes_needed(int64_t n, int d)
     b += 2 * (size_t)n * 8 + 2 * (size_t)n * 4;  // keys, perm (+ alternates)
     b += 16 * ((size_t)n + 1) * 4;           // active lists, flags, scans, groups, fail
     b += (size_t)n * 8;                      // work items
-    b += H * 16;                             // hash map
+    b += 4 * H * 16;                         // cell hash maps of up to four grid levels
+    b += 3 * (size_t)n * 4 + 2 * (size_t)n;  // levels, level sort keys, window minima
     b += 256 * (((size_t)n + RS_TILE - 1) / RS_TILE) * 4 + 64 * 1024;  // histograms, sums, small
     b += sizeof(PrepReduce) + sizeof(GridParams) + 64 * 256;          // alignment slack
     return b;
@@ -979,13 +1036,9 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
         P.evs[1] = D.ev[4];
         // Reserve the buffers whose size varies between passes at their
         // largest, so no buffer is carved twice.
-        size_t H = 1;
-        while (H < (size_t)(2 * n)) H <<= 1;
         const char *per_point[] = {"gbegin", "skey", "sval", "skey2", "sval2", "nit", "ioff", "fail", "fpos"};
         for (const char *nm : per_point) P.sc.get<uint32_t>(nm, (size_t)n + 1);
         P.sc.get<uint2>("items", (size_t)n + 1);
-        P.sc.get<uint64_t>("hkey", H);
-        P.sc.get<uint2>("hval", H);
         P.sc.get<uint32_t>("scan_sums0", (size_t)(n + SCAN_TILE - 1) / SCAN_TILE + 2);
         P.sc.get<uint32_t>("scan_sums1", 4);
         P.run(points, n, d, K, out_ids, out_dist);

@@ -40,19 +40,18 @@ struct ScanArgs {
     const uint32_t *perm;      // key order -> original id
     const uint64_t *keys;      // sorted Morton keys
     const uint32_t *active;    // active list (sorted positions)
-    const uint2 *items;        // (first active index, count)
+    const uint2 *items;        // (first active index, count | level << 16)
     uint32_t nitems;
     uint32_t *counter;         // work-queue head
-    const uint64_t *hkey;      // level hash map
-    const uint2 *hval;
-    uint32_t hmask;
+    const uint64_t *hkeyL[MAX_LEVELS];  // per-level hash maps (cell key -> run)
+    const uint2 *hvalL[MAX_LEVELS];
+    uint32_t hmaskL[MAX_LEVELS];
     uint32_t *fail;            // [n] per sorted position: 0 certified, 1 not, 2 overflow
     int32_t *out_ids;          // [n][K]
     double *out_dist;          // [n][K]
     unsigned long long *stats; // [0] candidates, [1] overflow rounds, [2] band entries
     int64_t n;
     int K;
-    int level;
     int bits;
     int cmax0[MAX_DIM];
     float lo[MAX_DIM];
@@ -154,7 +153,7 @@ __device__ __forceinline__ uint64_t exact_d2(const float *q, const int32_t *qi, 
         uint64_t bits;
         if (canon_d2_fixed<DIM>(qi, ci, a.F, bits)) return bits;
     }
-    return canon_d2_general<DIM>(q, c);
+    return canon_d2_fp64<DIM>(q, c);
 }
 
 __device__ __forceinline__ bool key_less(uint64_t da, uint32_t ia, uint64_t db, uint32_t ib)
@@ -191,11 +190,6 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
     uint64_t *wxk = xkey + warp * B;
     uint32_t *wxi = xid + warp * B, *wxs = xs_ + warp * B;
 
-    const int shift = DIM * a.level;
-    const int nbits = a.bits - a.level;
-    int cmaxL[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) cmaxL[k] = a.cmax0[k] >> a.level;
     unsigned long long st_cand = 0, st_ovf = 0, st_band = 0;
 
     for (;;) {
@@ -204,7 +198,13 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
         const int item = s_item;
         if ((uint32_t)item >= a.nitems) break;
         const uint2 it = a.items[item];
-        const bool has_q = (uint32_t)warp < it.y;
+        const int level = (int)(it.y >> 16);
+        const int shift = DIM * level;
+        const int nbits = a.bits - level;
+        int cmaxL[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cmaxL[k] = a.cmax0[k] >> level;
+        const bool has_q = (uint32_t)warp < (it.y & 0xffffu);
         const uint32_t qa = it.x + warp;
         const uint32_t qs = has_q ? a.active[qa] : 0u;
 
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 ok = ok && nb[k] >= 0 && nb[k] <= cmaxL[k];
             }
             uint2 rg = make_uint2(0, 0);
-            if (ok) rg = hash_lookup(a.hkey, a.hval, a.hmask, morton_encode(nb, DIM, nbits));
+            if (ok) rg = hash_lookup(a.hkeyL[level], a.hvalL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
             nb_range[t] = rg;
         }
         __syncthreads();
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                                 float c[DIM];
 #pragma unroll
                                 for (int k = 0; k < DIM; ++k) c[k] = cx[k * CH + t];
-                                D = canon_d2_general<DIM>(q, c);
+                                D = canon_d2_fp64<DIM>(q, c);
                                 id = a.perm[s];
                             }
                             bool acc = valid && key_less(D, id, thrD, thrI);
@@ -434,11 +434,11 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
             for (int k = 0; k < DIM; ++k) {
                 int cL = s_cell[k];
                 if (cL >= 2) {
-                    float f = face_of((cL - 1) << a.level, a.lo[k], a.w0);
+                    float f = face_of((cL - 1) << level, a.lo[k], a.w0);
                     R = fminf(R, __fsub_rd(q[k], f));
                 }
                 if (cL + 1 < cmaxL[k]) {
-                    float f = face_of((cL + 2) << a.level, a.lo[k], a.w0);
+                    float f = face_of((cL + 2) << level, a.lo[k], a.w0);
                     R = fminf(R, __fsub_rd(f, q[k]));
                 }
             }

@@ -302,14 +302,14 @@ __device__ __forceinline__ float dist2_f32(const float (&q)[DIM], const float (&
 // down): distance to the nearest face of the 3^d box beyond which points exist.
 template <int DIM>
 __device__ __forceinline__ float cert_radius(const float *q, const int *cell, const int *cmaxL,
-                                             const ScanArgs &a)
+                                             const ScanArgs &a, int level)
 {
     float R = __int_as_float(0x7f800000);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const int cL = cell[k];
-        if (cL >= 2) R = fminf(R, __fsub_rd(q[k], face_of((cL - 1) << a.level, a.lo[k], a.w0)));
-        if (cL + 1 < cmaxL[k]) R = fminf(R, __fsub_rd(face_of((cL + 2) << a.level, a.lo[k], a.w0), q[k]));
+        if (cL >= 2) R = fminf(R, __fsub_rd(q[k], face_of((cL - 1) << level, a.lo[k], a.w0)));
+        if (cL + 1 < cmaxL[k]) R = fminf(R, __fsub_rd(face_of((cL + 2) << level, a.lo[k], a.w0), q[k]));
     }
     return R;
 }
@@ -347,11 +347,6 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
     uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
     uint32_t *hist = qsv + QM;                 // [256]
 
-    const int shift = DIM * a.level;
-    const int nbits = a.bits - a.level;
-    int cmaxL[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) cmaxL[k] = a.cmax0[k] >> a.level;
     unsigned long long st_cand = 0, st_band = 0;
     KNN_PT_DECL;
 
@@ -361,7 +356,16 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
         item = __shfl_sync(FULL, item, 0);
         if (item >= a.nitems) break;
         const uint2 it = a.items[item];
-        const int Q = (int)it.y;
+        const int Q = (int)(it.y & 0xffffu);
+        const int level = (int)(it.y >> 16);
+        const int shift = DIM * level;
+        const int nbits = a.bits - level;
+        int cmaxL[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cmaxL[k] = a.cmax0[k] >> level;
+        const uint64_t *hkey = a.hkeyL[level];
+        const uint2 *hval = a.hvalL[level];
+        const uint32_t hmask = a.hmaskL[level];
 
         if (lane < Q) {
             uint32_t s = a.active[it.x + lane];
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
             float q[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
-            const float R = cert_radius<DIM>(q, cell, cmaxL, a);
+            const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
             qc[lane * QP + DIM] = isinf(R) ? __int_as_float(0x7f800000)
                                            : __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-14f);
             qc[lane * QP + DIM + 1] = __uint_as_float(qsv[lane]);
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                     ok = ok && nb[k] >= 0 && nb[k] <= cmaxL[k];
                 }
                 if (ok) {
-                    uint2 rg = hash_lookup(a.hkey, a.hval, a.hmask, morton_encode(nb, DIM, nbits));
+                    uint2 rg = hash_lookup(hkey, hval, hmask, morton_encode(nb, DIM, nbits));
                     rb = rg.x;
                     re = rg.y;
                 }
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                             for (int k = 0; k < DIM; ++k) ci[k] = to_fixed(c[k], a.F);
                             done = canon_d2_fixed<DIM>(qi, ci, a.F, bits);
                         }
-                        if (!done) bits = canon_d2_general<DIM>(q, c);
+                        if (!done) bits = canon_d2_fp64<DIM>(q, c);
                         D[e] = bits;
                         I[e] = a.perm[s];
                     }
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 for (int e = 0; e < E; ++e)
                     if (e == (K - 1) % E) dk = D[e];
                 dk = __shfl_sync(FULL, dk, (K - 1) / E);
-                const float R = cert_radius<DIM>(q, cell, cmaxL, a);
+                const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
                 bool certified = isinf(R);
                 if (!certified) {
                     const float R2 = __fmul_rd(__fmul_rd(R, R), 1.0f - 0x1p-20f);
