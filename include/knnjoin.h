@@ -65,11 +65,12 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *user);  /* optional device allocator */
     void (*free)(void *ptr, void *user);       /* matching free */
     void *user;
-    size_t hbm_budget_bytes;  /* serving admission limit; 0 = 90% of free memory */
-    int max_jobs;             /* serving queue slots; 0 = 64 */
+    size_t hbm_budget_bytes;  /* admission limit of batched/served jobs; 0 = 90% of free memory */
+    int max_jobs;             /* serving queue slots (jobs waiting to start); 0 = 1024 */
     const char *tune_cache_path; /* reserved */
     float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.3); 0 = default */
-    int reserved[8];
+    int workers;              /* concurrent join pipelines for batched/served jobs; 0 = 8 */
+    int reserved[7];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */
@@ -100,6 +101,8 @@ typedef struct {
     double ms_index;               /* device time up to the first pass */
     double ms_scan;                /* device time of the scan kernel launches */
     int64_t launches;              /* kernel launches of the join */
+    double ms_queue;               /* served/batched: submit -> start (host clock) */
+    double ms_wall;                /* served/batched: submit -> done (host clock) */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).
@@ -122,12 +125,19 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
                                  int32_t *out_ids, double *out_dist);
 
 /* Blocking: run njobs independent self-joins (same conventions as
- * knnjoin_self_join per job).  Returns the first failing job's status. */
+ * knnjoin_self_join per job) concurrently on the context's worker pipelines
+ * (each its own stream and scratch), admitted by device-memory footprint.
+ * Work queued on the context's stream before the call completes first.
+ * Returns the first failing job's status. */
 knnjoin_status knnjoin_self_join_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs, int njobs);
 
-/* Serving: enqueue a join and return at once with *job_id.  The caller keeps
- * the job's buffers alive until knnjoin_poll returns a status other than
- * KNN_ERR_NOT_READY.  KNN_ERR_QUEUE_FULL if no slot is free. */
+/* Serving: enqueue a join and return at once with *job_id.  Jobs start in
+ * arrival order as soon as a worker pipeline is free and the job's device
+ * memory footprint fits the budget beside the running ones (continuous
+ * batching: jobs overlap on the GPU).  The caller keeps the job's buffers
+ * alive until knnjoin_poll returns a status other than KNN_ERR_NOT_READY.
+ * KNN_ERR_QUEUE_FULL if max_jobs jobs are already waiting; KNN_ERR_INVALID
+ * for bad arguments (checked at submission). */
 knnjoin_status knnjoin_submit(knnjoin_ctx *ctx, const knnjoin_job *job, uint64_t *job_id);
 
 /* KNN_OK when the job finished, KNN_ERR_NOT_READY while it runs, else its

@@ -40,7 +40,7 @@ class KnnjoinConfig(ctypes.Structure):
                 ("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("user", ctypes.c_void_p),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
                 ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
-                ("reserved", ctypes.c_int * 8)]
+                ("workers", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class KnnjoinJob(ctypes.Structure):
@@ -57,7 +57,8 @@ class KnnjoinStats(ctypes.Structure):
                 ("cell_width", ctypes.c_double), ("key_bits", ctypes.c_int),
                 ("fixed_point", ctypes.c_int), ("ms_total", ctypes.c_double),
                 ("ms_index", ctypes.c_double), ("ms_scan", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("ms_queue", ctypes.c_double),
+                ("ms_wall", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -194,7 +195,7 @@ class Context:
     current stream on it."""
 
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
-                 max_jobs: int = 0, hbm_budget_bytes: int = 0):
+                 max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -209,6 +210,7 @@ class Context:
         cfg.width_mult = width_mult
         cfg.max_jobs = max_jobs
         cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.workers = workers
         self._cfg = cfg
         self.ctx = knnjoin_create(cfg)
 

@@ -651,55 +651,98 @@ void validate(const float *points, int64_t n, int d, int K, const int32_t *ids, 
 // ---------------------------------------------------------------------------
 // Context and serving queue
 // ---------------------------------------------------------------------------
+// Job of the serving queue (or one job of a blocking batch).
+struct Batch {
+    int left = 0;
+    knnjoin_status first = KNN_OK;
+    std::string err;
+};
+
 struct Job {
-    uint64_t id;
-    knnjoin_job job;
+    uint64_t id = 0;
+    knnjoin_job job{};
     std::atomic<int> state{0};  // 0 queued, 1 running, 2 done, 3 cancelled
     knnjoin_status status = KNN_OK;
     std::string err;
     knnjoin_stats stats{};
+    size_t footprint = 0;
+    std::shared_ptr<Batch> batch;  // set for jobs of a blocking batch
+    std::chrono::steady_clock::time_point t_submit, t_start, t_end;
+};
+
+// A worker: its own stream, scratch and host thread; workers run jobs
+// concurrently so one job's host round trips and small kernels overlap with
+// another's scan.
+struct Worker {
+    Pipeline pipe;
+    cudaStream_t stream = nullptr;
+    std::thread th;
 };
 
 struct knnjoin_ctx {
     int device = 0;
-    cudaStream_t stream = nullptr, serve_stream = nullptr;
+    cudaStream_t stream = nullptr;
     bool own_stream = false;
     Allocator al;
-    Pipeline main, serve;
+    Pipeline main;
     std::string err;
     knnjoin_config cfg{};
-    // serving
+    // worker pool (batched and served joins)
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Job>> queue;
     std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
+    std::vector<std::unique_ptr<Worker>> workers;
     uint64_t next_id = 1;
-    std::thread worker;
     bool stop = false;
-    bool worker_started = false;
-    int max_jobs = 64;
+    int nworkers = 8;
+    int max_jobs = 1024;
+    size_t budget = 0, in_use = 0;
 };
 
-static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f);
+// Device memory a join of n points holds while it runs (an estimate: the
+// scratch of one pipeline, two levels of cell maps, and staging copies of
+// host buffers).
+static size_t job_footprint(const knnjoin_job &j)
+{
+    const size_t n = (size_t)std::max<int64_t>(j.n, 0);
+    size_t H = 1;
+    while (H < 2 * n) H <<= 1;
+    size_t b = n * (size_t)(4 * j.d + 4 * pad_dim(std::max(1, std::min(j.d, MAX_DIM))) + 24 + 72) + 2 * H * 16;
+    if (!is_device_ptr(j.points)) b += n * (size_t)j.d * 4;
+    if (!is_device_ptr(j.out_ids)) b += n * (size_t)j.K * 4;
+    if (!is_device_ptr(j.out_dist)) b += n * (size_t)j.K * 8;
+    return b + ((size_t)1 << 20);
+}
 
-static void serve_loop(knnjoin_ctx *ctx)
+static void worker_loop(knnjoin_ctx *ctx, Worker *w)
 {
     for (;;) {
         std::shared_ptr<Job> j;
         {
             std::unique_lock<std::mutex> lk(ctx->mu);
-            ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
-            if (ctx->stop) return;
+            for (;;) {
+                if (ctx->stop) return;
+                while (!ctx->queue.empty() && ctx->queue.front()->state.load() == 3) ctx->queue.pop_front();
+                if (!ctx->queue.empty()) {
+                    auto &f = ctx->queue.front();
+                    // admission by HBM footprint (the head of the queue waits
+                    // until it fits; a job runs alone if it never fits)
+                    if (ctx->in_use == 0 || ctx->in_use + f->footprint <= ctx->budget) break;
+                }
+                ctx->cv.wait(lk);
+            }
             j = ctx->queue.front();
             ctx->queue.pop_front();
-            int expect = 0;
-            if (!j->state.compare_exchange_strong(expect, 1)) continue;  // cancelled
+            j->state.store(1);
+            ctx->in_use += j->footprint;
+            j->t_start = std::chrono::steady_clock::now();
         }
         knnjoin_status st = KNN_OK;
         std::string msg;
         try {
             validate(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
-            ctx->serve.run(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
+            w->pipe.run(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
         } catch (const KnnError &e) {
             st = e.st;
             msg = e.msg;
@@ -709,11 +752,42 @@ static void serve_loop(knnjoin_ctx *ctx)
         }
         {
             std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->in_use -= j->footprint;
+            j->t_end = std::chrono::steady_clock::now();
             j->status = st;
             j->err = msg;
-            j->stats = ctx->serve.stats;
+            j->stats = w->pipe.stats;
+            j->stats.ms_queue = std::chrono::duration<double, std::milli>(j->t_start - j->t_submit).count();
+            j->stats.ms_wall = std::chrono::duration<double, std::milli>(j->t_end - j->t_submit).count();
+            if (j->batch) {
+                if (st != KNN_OK && j->batch->first == KNN_OK) {
+                    j->batch->first = st;
+                    j->batch->err = msg;
+                }
+                j->batch->left--;
+            }
             j->state.store(2);
         }
+        ctx->cv.notify_all();
+    }
+}
+
+static void start_workers(knnjoin_ctx *ctx)
+{
+    if (!ctx->workers.empty()) return;
+    for (int i = 0; i < ctx->nworkers; ++i) {
+        auto w = std::make_unique<Worker>();
+        CK(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+        w->pipe.init(ctx->device, w->stream, &ctx->al);
+        w->pipe.width_mult = ctx->main.width_mult;
+        ctx->workers.push_back(std::move(w));
+    }
+    for (auto &w : ctx->workers) {
+        Worker *wp = w.get();
+        w->th = std::thread([ctx, wp] {
+            cudaSetDevice(ctx->device);
+            worker_loop(ctx, wp);
+        });
     }
 }
 
@@ -771,19 +845,18 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
             CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
             ctx->own_stream = true;
         }
-        CK(cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking));
         ctx->al.alloc = ctx->cfg.alloc;
         ctx->al.free = ctx->cfg.free;
         ctx->al.user = ctx->cfg.user;
         if ((ctx->al.alloc == nullptr) != (ctx->al.free == nullptr))
             fail(KNN_ERR_INVALID, "alloc and free hooks must be given together");
         ctx->main.init(ctx->device, ctx->stream, &ctx->al);
-        ctx->serve.init(ctx->device, ctx->serve_stream, &ctx->al);
-        if (ctx->cfg.width_mult > 0.0f) {
-            ctx->main.width_mult = ctx->cfg.width_mult;
-            ctx->serve.width_mult = ctx->cfg.width_mult;
-        }
+        if (ctx->cfg.width_mult > 0.0f) ctx->main.width_mult = ctx->cfg.width_mult;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
+        if (ctx->cfg.workers > 0) ctx->nworkers = std::min(ctx->cfg.workers, 64);
+        size_t freeb = 0, totalb = 0;
+        CK(cudaMemGetInfo(&freeb, &totalb));
+        ctx->budget = ctx->cfg.hbm_budget_bytes ? ctx->cfg.hbm_budget_bytes : (size_t)(0.9 * (double)freeb);
     });
     if (st != KNN_OK) {
         knnjoin_destroy(ctx);
@@ -801,14 +874,17 @@ void knnjoin_destroy(knnjoin_ctx *ctx)
         ctx->stop = true;
     }
     ctx->cv.notify_all();
-    if (ctx->worker.joinable()) ctx->worker.join();
+    for (auto &w : ctx->workers)
+        if (w->th.joinable()) w->th.join();
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->serve_stream) cudaStreamSynchronize(ctx->serve_stream);
+    for (auto &w : ctx->workers) {
+        cudaStreamSynchronize(w->stream);
+        w->pipe.release();
+        cudaStreamDestroy(w->stream);
+    }
     ctx->main.release();
-    ctx->serve.release();
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
-    if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
     delete ctx;
 }
 
@@ -829,8 +905,28 @@ knnjoin_status knnjoin_self_join_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs
         if (njobs < 0 || (njobs > 0 && !jobs)) fail(KNN_ERR_INVALID, "bad job list");
         for (int i = 0; i < njobs; ++i)
             validate(jobs[i].points, jobs[i].n, jobs[i].d, jobs[i].K, jobs[i].out_ids, jobs[i].out_dist);
-        for (int i = 0; i < njobs; ++i)
-            ctx->main.run(jobs[i].points, jobs[i].n, jobs[i].d, jobs[i].K, jobs[i].out_ids, jobs[i].out_dist);
+        if (njobs == 0) return;
+        // the caller's stream may hold work producing the inputs
+        CK(cudaStreamSynchronize(ctx->stream));
+        auto b = std::make_shared<Batch>();
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            start_workers(ctx);
+            b->left = njobs;
+            const auto now = std::chrono::steady_clock::now();
+            for (int i = 0; i < njobs; ++i) {
+                auto j = std::make_shared<Job>();
+                j->job = jobs[i];
+                j->footprint = job_footprint(jobs[i]);
+                j->batch = b;
+                j->t_submit = now;
+                ctx->queue.push_back(j);
+            }
+        }
+        ctx->cv.notify_all();
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        ctx->cv.wait(lk, [&] { return b->left == 0; });
+        if (b->first != KNN_OK) fail(b->first, b->err);
     });
 }
 
@@ -839,19 +935,22 @@ knnjoin_status knnjoin_submit(knnjoin_ctx *ctx, const knnjoin_job *job, uint64_t
     if (!ctx) return KNN_ERR_INVALID;
     return guard(ctx, [&] {
         if (!job || !job_id) fail(KNN_ERR_INVALID, "NULL job or job_id");
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        if ((int)ctx->queue.size() >= ctx->max_jobs) fail(KNN_ERR_QUEUE_FULL, "serving queue is full");
-        auto j = std::make_shared<Job>();
-        j->id = ctx->next_id++;
-        j->job = *job;
-        ctx->jobs[j->id] = j;
-        ctx->queue.push_back(j);
-        *job_id = j->id;
-        if (!ctx->worker_started) {
-            ctx->worker = std::thread(serve_loop, ctx);
-            ctx->worker_started = true;
+        validate(job->points, job->n, job->d, job->K, job->out_ids, job->out_dist);
+        const size_t fp = job_footprint(*job);
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            if ((int)ctx->queue.size() >= ctx->max_jobs) fail(KNN_ERR_QUEUE_FULL, "serving queue is full");
+            start_workers(ctx);
+            auto j = std::make_shared<Job>();
+            j->id = ctx->next_id++;
+            j->job = *job;
+            j->footprint = fp;
+            j->t_submit = std::chrono::steady_clock::now();
+            ctx->jobs[j->id] = j;
+            ctx->queue.push_back(j);
+            *job_id = j->id;
         }
-        ctx->cv.notify_one();
+        ctx->cv.notify_all();
     });
 }
 

@@ -55,10 +55,10 @@ def test_struct_layouts_match_header(tmp_path):
                  for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                          check=True).stdout.splitlines())
     assert lines["config"] == [ctypes.sizeof(kj.KnnjoinConfig), kj.KnnjoinConfig.width_mult.offset,
-                               kj.KnnjoinConfig.hbm_budget_bytes.offset]
+                               kj.KnnjoinConfig.hbm_budget_bytes.offset, kj.KnnjoinConfig.workers.offset]
     assert lines["job"] == [ctypes.sizeof(kj.KnnjoinJob), kj.KnnjoinJob.out_dist.offset]
     assert lines["stats"] == [ctypes.sizeof(kj.KnnjoinStats), kj.KnnjoinStats.candidates.offset,
-                              kj.KnnjoinStats.ms_index.offset]
+                              kj.KnnjoinStats.ms_index.offset, kj.KnnjoinStats.ms_wall.offset]
 
 
 def test_exact_arithmetic_matches_ieee_double_on_host(tmp_path):
