@@ -1,7 +1,7 @@
 """Benchmark of the exact KNN self-join on B300 (one JSON line on stdout).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload unif|expo] [--no-cpu-baseline] [--no-e2e]
+                    [--workload unif|expo|batched|served] [--no-cpu-baseline] [--no-e2e]
 
 A step is one pass of the whole join -- search-distance selection, grid
 index, density queue, every scan pass and the output -- over each point set
@@ -24,10 +24,20 @@ those bytes / the scan kernel's event-timed duration.
 
 --impl reference times the CPU oracle (exact grid join, OpenMP on the host
 cores) on a bounded sample of the same workload per step.
+
+--workload batched: 256 independent joins (n log-uniform in [1k, 200k], d in
+{2,3,4,6}, K in {4..64}, uniform or exponential(40)) through
+knnjoin_self_join_batch (worker pool, concurrent) against a plain loop of
+knnjoin_self_join calls on one stream; both timed per step, results equal.
+--workload served: a Poisson stream of joins (n log-uniform in [10k, 5M],
+d 2..6, K 8..128, uniform / exponential(40) / clustered 2-D) submitted and
+polled through knnjoin_submit/knnjoin_poll at rho x the measured capacity;
+p50/p99 latency (submit -> done) against FIFO one-at-a-time serving.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -379,13 +389,176 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched and served workloads
+# ---------------------------------------------------------------------------
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import paper_1810_04758_b300 as kj
+    from paper_1810_04758_b300 import build as kbuild
+
+    kbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    jobs = gen.batched_jobs(args.jobs or 256, seed=0)
+    pts = [torch.from_numpy(gen.batched_points(j)).to(dev) for j in jobs]
+    Ks = [j["K"] for j in jobs]
+    nq = sum(len(p) for p in pts)
+    outs_a = [(torch.empty((len(p), K), dtype=torch.int32, device=dev),
+               torch.empty((len(p), K), dtype=torch.float64, device=dev)) for p, K in zip(pts, Ks)]
+    outs_b = [(torch.empty_like(a), torch.empty_like(b)) for a, b in outs_a]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = kj.Context(device=local_rank, stream=stream, workers=args.workers)
+
+    def plain():
+        for p, K, (i, d) in zip(pts, Ks, outs_a):
+            ctx.self_join(p, K, i, d)
+
+    def batched():
+        jl = [kj.KnnjoinJob(p.data_ptr(), len(p), p.shape[1], K, i.data_ptr(), d.data_ptr())
+              for p, K, (i, d) in zip(pts, Ks, outs_b)]
+        kj.knnjoin_self_join_batch(ctx.ctx, jl)
+
+    def timed(fn):
+        ms = []
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    with ClockSampler(local_rank) as clk:
+        ms_plain = timed(plain)
+        ms_batch = timed(batched)
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs_a, outs_b))
+    ctx.close()
+    if rank != 0:
+        return 0
+    value = world * nq / (ms_batch / 1e3)
+    line = {
+        "metric": "batched query points/s (256 joins, n 1k-200k, d 2-6, K 4-64)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (scan) + exact canonical-f64 re-score", "data": "synthetic",
+        "config": {"workload": f"Batched: {len(jobs)} joins, {nq} points in all, n log-uniform "
+                               f"[1k,200k], d in {{2,3,4,6}}, K in {{4,8,16,32,64}}, uniform or "
+                               f"exponential(40), seed 0", "workers": args.workers or 8,
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "plain_per_job": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                          "how": "knnjoin_self_join per job, sequentially on one stream"},
+        "speedup_vs_plain": ms_plain / ms_batch,
+        "results_identical_to_plain": bool(same),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args, rank, world, local_rank):
+    import torch
+    import paper_1810_04758_b300 as kj
+    from paper_1810_04758_b300 import build as kbuild
+
+    kbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    jobs = gen.served_jobs(args.jobs or 120, seed=0)
+    pts = [torch.from_numpy(gen.served_points(j)).to(dev) for j in jobs]
+    Ks = [j["K"] for j in jobs]
+    outs = [(torch.empty((len(p), K), dtype=torch.int32, device=dev),
+             torch.empty((len(p), K), dtype=torch.float64, device=dev)) for p, K in zip(pts, Ks)]
+    nq = sum(len(p) for p in pts)
+    torch.cuda.synchronize()
+
+    def serve(workers, rate):
+        """Submit job k at its Poisson arrival time (rate jobs/s; 0 = all at
+        once), poll until done; returns (makespan s, latencies ms)."""
+        ctx = kj.Context(device=local_rank, workers=workers)
+        # warm the worker pipelines
+        for k in range(min(len(jobs), workers)):
+            ctx.self_join(pts[k][:2000].contiguous(), min(Ks[k], 1999))
+        u = np.array([j["u_arrival"] for j in jobs])
+        gaps = -np.log1p(-u) / rate if rate > 0 else np.zeros(len(jobs))
+        arrivals = np.cumsum(gaps)
+        pending, lat = {}, {}
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(jobs) or pending:
+            now = time.perf_counter() - t0
+            while k < len(jobs) and arrivals[k] <= now:
+                jid, _, _ = ctx.submit(pts[k], Ks[k], *outs[k])
+                pending[jid] = k
+                k += 1
+            for jid in list(pending):
+                # a finished job has its wall time set; read it, then retire
+                # the job with the final poll
+                stats = kj.KnnjoinStats()
+                rc = kj.load_library().knnjoin_get_stats(ctx.ctx, jid, ctypes.byref(stats))
+                if rc != 0 or stats.ms_wall <= 0:
+                    continue
+                st = ctx.poll(jid)
+                if st != kj.KNN_OK:
+                    raise RuntimeError(f"job failed: {ctx.last_error()}")
+                lat[pending.pop(jid)] = stats.ms_wall
+            time.sleep(0.0002)
+        span = time.perf_counter() - t0
+        ctx.close()
+        return span, lat
+
+    span_cap, _ = serve(args.workers or 8, 0.0)
+    capacity = len(jobs) / span_cap
+    results = {}
+    for rho in (0.5, 0.8, 0.95):
+        rate = rho * capacity
+        span, lat = serve(args.workers or 8, rate)
+        span1, lat1 = serve(1, rate)
+        lv = sorted(v for v in lat.values() if v is not None)
+        lv1 = sorted(v for v in lat1.values() if v is not None)
+        pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
+        results[str(rho)] = {"arrival_jobs_per_s": rate,
+                             "p50_ms": pct(lv, 0.5), "p99_ms": pct(lv, 0.99),
+                             "q_per_s": nq / span,
+                             "fifo_p50_ms": pct(lv1, 0.5), "fifo_p99_ms": pct(lv1, 0.99),
+                             "fifo_q_per_s": nq / span1}
+    if rank != 0:
+        return 0
+    top = results["0.95"]
+    line = {
+        "metric": "served query points/s at rho=0.95 with p50/p99 latency (Poisson join stream)",
+        "value": world * top["q_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": span_cap * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (scan) + exact canonical-f64 re-score", "data": "synthetic",
+        "config": {"workload": f"Served: {len(jobs)} joins, {nq} points in all, n log-uniform "
+                               f"[10k,5M], d 2..6, K log-uniform [8,128], 1/3 uniform, 1/3 "
+                               f"exponential(40), 1/3 clustered 2-D; Poisson arrivals at rho x "
+                               f"capacity", "workers": args.workers or 8},
+        "capacity_jobs_per_s": capacity,
+        "by_rho": results,
+        "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+        "fifo_baseline": {"q_per_s": top["fifo_q_per_s"], "p50_ms": top["fifo_p50_ms"],
+                          "p99_ms": top["fifo_p99_ms"], "how": "one worker: FIFO one job at a time"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="unif")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served"], default="unif")
+    ap.add_argument("--jobs", type=int, default=0, help="batched/served: number of joins")
+    ap.add_argument("--workers", type=int, default=0, help="batched/served: worker pipelines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
@@ -398,7 +571,15 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.workload in ("batched", "served"):
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the CPU oracle is timed on the unif/expo workloads only"}))
+            return 0
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world, local_rank)
+    if args.workload == "served":
+        return run_served(args, rank, world, local_rank)
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
