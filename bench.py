@@ -141,6 +141,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device, world: int) -> float:
+    """Maximum of a per-rank value over all ranks (the job's time is the
+    slowest rank's); identity on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algorithmic_bytes(name: str, n: int, d: int, K: int, wref: dict) -> tuple[float, float]:
     """(bytes, fp32 flops) of one join at the roofline, from W_ref."""
     w = wref.get(name, {}).get("candidates")
@@ -284,11 +296,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev, world)
     nq_step = sum(len(hosts[nm][0]) for nm in names)
     ms_per_step = total_ms / args.steps
     value = world * nq_step / (ms_per_step / 1000.0)
