@@ -271,7 +271,7 @@ int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 size_t scan2_smem_bytes(int d, int QM, int E)
 {
     const int BS = 32 * E, QP = query_row_floats(d);
-    size_t w = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4;
+    size_t w = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4 + (size_t)QM * 2 * d * 4;
     return (size_t)S2_WARPS * ((w + 15) & ~(size_t)15);
 }
 

@@ -298,6 +298,41 @@ __device__ __forceinline__ float dist2_f32(const float (&q)[DIM], const float (&
     return e + o;
 }
 
+// Bitonic sort, ascending, of 32*E 32-bit values held E per lane in blocked
+// order (entry g = lane*E + e).
+template <int E>
+__device__ __forceinline__ void warp_bitonic_u32(uint32_t (&V)[E], int lane)
+{
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int p = e ^ j;
+                    if (p > e) {
+                        const bool up = ((lane * E + e) & k) == 0;
+                        const uint32_t lo = min(V[e], V[p]), hi = max(V[e], V[p]);
+                        V[e] = up ? lo : hi;
+                        V[p] = up ? hi : lo;
+                    }
+                }
+            } else {
+                const int lm = j / E;
+                const bool lower = (lane & lm) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t o = __shfl_xor_sync(FULL, V[e], lm);
+                    const bool up = ((lane * E + e) & k) == 0;
+                    V[e] = (lower == up) ? min(o, V[e]) : max(o, V[e]);
+                }
+            }
+        }
+    }
+}
+
 // Certificate radius of a query at level `level` in cell `cell` (rounded
 // down): distance to the nearest face of the 3^d box beyond which points exist.
 template <int DIM>
@@ -339,13 +374,15 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
 
     // per-warp shared memory
     constexpr int BS = B;
-    const size_t wbytes = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4;
+    const size_t wbytes = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4 +
+                          (size_t)QM * 2 * DIM * 4;
     unsigned char *wb = smem + warp * ((wbytes + 15) & ~(size_t)15);
     uint64_t *buf = (uint64_t *)wb;            // [QM][BS]  (d2_32 bits << 32 | sorted index)
     float *qc = (float *)(buf + QM * BS);      // [QM][QP] coords, threshold, sorted position
     int *cnt = (int *)(qc + QM * QP);          // [QM]
     uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
     uint32_t *hist = qsv + QM;                 // [256]
+    float *gaps = (float *)(hist + 256);       // [QM][2*DIM] distance to own cell's faces (rounded down)
 
     unsigned long long st_cand = 0, st_band = 0;
     KNN_PT_DECL;
@@ -387,6 +424,11 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
 #pragma unroll
             for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
             const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                gaps[lane * 2 * DIM + 2 * k] = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
+                gaps[lane * 2 * DIM + 2 * k + 1] = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
+            }
             qc[lane * QP + DIM] = isinf(R) ? __int_as_float(0x7f800000)
                                            : __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-14f);
             qc[lane * QP + DIM + 1] = __uint_as_float(qsv[lane]);
@@ -398,9 +440,11 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
         for (int ob = 0; ob < NOFF; ob += 32) {
             const int o = ob + lane;
             uint32_t rb = 0, re = 0;
+            int code = 0;
             if (o < NOFF) {
                 int nb[DIM];
                 int r = c_nb_order[nb_order_offset(DIM) + o];
+                code = r;
                 bool ok = true;
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
@@ -415,6 +459,26 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 }
             }
             const uint32_t len = re - rb;
+            // queries this cell can still serve: rounded-down squared distance
+            // from the query to the cell's box, against the query's threshold
+            // with a 2^-19 margin for FP32 rounding of candidate distances
+            uint32_t cmask = 0;
+            if (len) {
+                for (int i = 0; i < Q; ++i) {
+                    float lb = 0.0f;
+                    int r = code;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        const int dg = r % 3;
+                        r /= 3;
+                        if (dg != 1) {
+                            const float g = gaps[i * 2 * DIM + 2 * k + (dg == 2 ? 1 : 0)];
+                            lb = __fmaf_rd(g, g, lb);
+                        }
+                    }
+                    if (!(lb > qc[i * QP + DIM] * (1.0f + 0x1p-19f))) cmask |= 1u << i;
+                }
+            }
             uint32_t inc = len;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -436,6 +500,8 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 const uint32_t sb = __shfl_sync(FULL, rb, src);
                 const uint32_t se = __shfl_sync(FULL, exc, src);
                 const uint32_t s = valid ? sb + (t - se) : 0u;
+                const uint32_t cm = __shfl_sync(FULL, cmask, src);  // every lane takes part
+                const uint32_t tmask = __reduce_or_sync(FULL, valid ? cm : 0u);
                 float c[DIM];
                 if (valid) {
                     load_point<DIM>(a.xsort, s, c);
@@ -446,6 +512,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 }
 #pragma unroll 2
                 for (int i = 0; i < Q; ++i) {
+                    if (!((tmask >> i) & 1u)) continue;
                     float qv[DIM], ti;
                     uint32_t qi_s;
                     load_query_row<DIM>(qc, i, qv, ti, qi_s);
@@ -494,25 +561,29 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 flag = 2;
             } else if (c0 >= K) {
                 const uint64_t *bi = buf + i * BS;
-                // whole buffer in registers, blocked (entry g = lane*E + e), sorted
-                // by (d2_32, index): T32 is entry K-1 and the band is a prefix
-                uint64_t v[E];
+                // whole buffer in registers (blocked: entry g = lane*E + e) as
+                // 32-bit words: the FP32 key with its low bits replaced by the
+                // buffer slot.  Sorted, entry K-1 bounds T32 from above by at
+                // most the dropped bits, and the band (a prefix) stays a
+                // superset of every entry within T32 (1 + 2^-15) + 2^-120.
+                constexpr uint32_t SLOT = (uint32_t)B - 1;
+                uint32_t v[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int g = lane * E + e;
-                    v[e] = g < c0 ? bi[g] : ~0ull;
+                    v[e] = g < c0 ? (((uint32_t)(bi[g] >> 32) & ~SLOT) | (uint32_t)g) : 0xffffffffu;
                 }
-                warp_bitonic_u64<E>(v, lane);
+                warp_bitonic_u32<E>(v, lane);
                 KNN_PT(3);
-                uint64_t vk = 0;
+                uint32_t vk = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e)
                     if (e == (K - 1) % E) vk = v[e];
                 vk = __shfl_sync(FULL, vk, (K - 1) / E);
-                const uint32_t tb = __float_as_uint(band_thr((uint32_t)(vk >> 32)));
+                const uint32_t tb = __float_as_uint(band_thr(vk | SLOT)) & ~SLOT;
                 int mine = 0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) mine += (lane * E + e < c0 && (uint32_t)(v[e] >> 32) <= tb) ? 1 : 0;
+                for (int e = 0; e < E; ++e) mine += (lane * E + e < c0 && (v[e] & ~SLOT) <= tb) ? 1 : 0;
                 int m = mine;
 #pragma unroll
                 for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(FULL, m, o);
@@ -533,7 +604,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                     D[e] = ~0ull;
                     I[e] = ~0u;
                     if (g < m) {
-                        const uint32_t s = (uint32_t)v[e];
+                        const uint32_t s = (uint32_t)bi[v[e] & SLOT];
                         float c[DIM];
                         load_point<DIM>(a.xsort, s, c);
                         uint64_t bits = 0;
