@@ -40,6 +40,7 @@ import argparse
 import ctypes
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -74,6 +75,36 @@ def peaks():
         return float(j["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+def csrc_digest() -> str:
+    """sha256 prefix over the library's CUDA sources (names and bytes)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1810_04758_b300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes (read + write) of the scan launches of one step, from the
+    committed ncu summary of this workload; None when there is none or the
+    CUDA sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_scan2_{workload}_2m.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"^traffic-bytes-per-step: (\d+)$", text, re.M)
+    h = re.search(r"^csrc-sha256-prefix: ([0-9a-f]+)$", text, re.M)
+    if not m or not h or h.group(1) != csrc_digest():
+        return None
+    return int(m.group(1))
 
 
 def wref_table():
@@ -322,6 +353,8 @@ def run_ours(args, rank, world, local_rank):
             "ms_scan": round(statistics.median(s["ms_scan"] for s in st), 4),
             "ms_index": round(statistics.median(s["ms_index"] for s in st), 4),
             "passes": st[-1]["passes"], "pass_queries": st[-1]["pass_queries"],
+            "ms_pass": [round(x, 3) for x in st[-1]["ms_pass"]],
+            "pass_candidates": st[-1]["pass_candidates"],
             "candidates": st[-1]["candidates"], "band_entries": st[-1]["band_entries"],
             "overflow_queries": st[-1]["overflow_queries"],
             "w_over_wref": (st[-1]["candidates"] / w_ref) if w_ref else None,
@@ -331,13 +364,17 @@ def run_ours(args, rank, world, local_rank):
     scan_ms_per_step = scan_ms / args.steps
     achieved = alg_bytes / (scan_ms_per_step / 1e3) / 1e9 if scan_ms_per_step > 0 else float("nan")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": "k_scan",
+                "frac": achieved / hbm, "traffic": None if args.configs else profiled_traffic(args.workload),
+                "kernel": "k_scan2",
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_step": alg_bytes,
                 "scan_ms_per_step": scan_ms_per_step,
                 "join_frac": roof_ms / ms_per_step,
                 "fp32_only_frac": (alg_flops / 69.2e12 * 1e3) / ms_per_step,
-                "note": "frac = scan-kernel achieved / measured HBM copy peak; join_frac = "
+                "note": "frac = scan-kernel achieved / measured HBM copy peak; algorithmic bytes "
+                        "credit no on-chip reuse (W_ref*4d), so frac > 1 where a candidate row "
+                        "serves several queries of an item; traffic = ncu DRAM bytes of the "
+                        "step's pass-1 scan launches (per step, like achieved); join_frac = "
                         "sum of per-join T_roof / whole-step device time"}
 
     # end to end through the C ABI with pinned host buffers

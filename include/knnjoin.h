@@ -103,6 +103,8 @@ typedef struct {
     int64_t launches;              /* kernel launches of the join */
     double ms_queue;               /* served/batched: submit -> start (host clock) */
     double ms_wall;                /* served/batched: submit -> done (host clock) */
+    double ms_pass[16];            /* device time of each pass's scan launches */
+    int64_t pass_candidates[16];   /* candidate distance evaluations of each pass */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).

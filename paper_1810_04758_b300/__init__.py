@@ -58,7 +58,9 @@ class KnnjoinStats(ctypes.Structure):
                 ("fixed_point", ctypes.c_int), ("ms_total", ctypes.c_double),
                 ("ms_index", ctypes.c_double), ("ms_scan", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("ms_queue", ctypes.c_double),
-                ("ms_wall", ctypes.c_double)]
+                ("ms_wall", ctypes.c_double),
+                ("ms_pass", ctypes.c_double * 16),
+                ("pass_candidates", ctypes.c_int64 * 16)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -66,6 +68,10 @@ class KnnjoinStats(ctypes.Structure):
             v = getattr(self, name)
             if name == "pass_queries":
                 v = [int(x) for x in v[: max(self.passes, 0)]]
+            elif name == "pass_candidates":
+                v = [int(x) for x in v[: max(min(self.passes, 16), 0)]]
+            elif name == "ms_pass":
+                v = [float(x) for x in v[: max(min(self.passes, 16), 0)]]
             d[name] = v
         return d
 

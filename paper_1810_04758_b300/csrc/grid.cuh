@@ -447,12 +447,13 @@ __global__ void k_run_begin(const uint32_t *__restrict__ flags, const uint32_t *
 }
 
 // Hash map (open addressing, linear probing) from level cell key to its run
-// [begin, end) in key order.  Capacity is a power of two >= 2 x cells.
+// [begin, end) in key order.  One 16-byte slot per entry -- key (x, y),
+// begin (z), end (w) -- so a probe is a single vector load.  Capacity is a
+// power of two >= 2 x cells.
 constexpr uint64_t HASH_EMPTY = ~0ull;
 
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
-                              const uint32_t *ncells_p, int shift, uint64_t *hkey, uint2 *hval,
-                              uint32_t hmask)
+                              const uint32_t *ncells_p, int shift, uint4 *slot, uint32_t hmask)
 {
     uint32_t ncells = *ncells_p;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
@@ -460,9 +461,9 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t 
         uint64_t P = keys[b] >> shift;
         uint32_t h = (uint32_t)mix64(P) & hmask;
         for (uint32_t probe = 0; probe <= hmask; ++probe) {
-            unsigned long long prev = atomicCAS((unsigned long long *)&hkey[h], HASH_EMPTY, P);
+            unsigned long long prev = atomicCAS((unsigned long long *)&slot[h], HASH_EMPTY, P);
             if (prev == HASH_EMPTY || prev == P) {
-                hval[h] = make_uint2(b, e);
+                ((uint2 *)&slot[h])[1] = make_uint2(b, e);
                 break;
             }
             h = (h + 1) & hmask;
@@ -470,13 +471,13 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t 
     }
 }
 
-__device__ __forceinline__ uint2 hash_lookup(const uint64_t *__restrict__ hkey, const uint2 *__restrict__ hval,
-                                             uint32_t hmask, uint64_t P)
+__device__ __forceinline__ uint2 hash_lookup(const uint4 *__restrict__ slot, uint32_t hmask, uint64_t P)
 {
     uint32_t h = (uint32_t)mix64(P) & hmask;
     for (uint32_t probe = 0; probe <= hmask; ++probe) {
-        uint64_t k = hkey[h];
-        if (k == P) return hval[h];
+        const uint4 v = __ldg(&slot[h]);
+        const uint64_t k = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        if (k == P) return make_uint2(v.z, v.w);
         if (k == HASH_EMPTY) break;
         h = (h + 1) & hmask;
     }

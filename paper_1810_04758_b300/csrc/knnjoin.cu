@@ -270,9 +270,7 @@ int bitlen32(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 
 size_t scan2_smem_bytes(int d, int QM, int E)
 {
-    const int BS = 32 * E, QP = query_row_floats(d);
-    size_t w = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4 + (size_t)QM * 2 * d * 4;
-    return (size_t)S2_WARPS * ((w + 15) & ~(size_t)15);
+    return (size_t)S2_WARPS * scan2_warp_bytes(d, QM, E);
 }
 
 // Fill the nearest-first neighbour order (scan2.cuh) on the current device.
@@ -299,7 +297,7 @@ void ensure_nb_order(int dev)
         std::stable_sort(v.begin(), v.end());
         for (auto &e : v) tab.push_back((uint16_t)e.second);
     }
-    CK(cudaMemcpyToSymbol(c_nb_order, tab.data(), tab.size() * sizeof(uint16_t)));
+    CK(cudaMemcpyToSymbol(g_nb_order, tab.data(), tab.size() * sizeof(uint16_t)));
     done[dev & 63] = true;
 }
 
@@ -451,6 +449,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
     uint32_t *small = sc.get<uint32_t>("small", 16);
     uint32_t *status = sc.get<uint32_t>("fail", n);  // per sorted position
+    float *seed = sc.get<float>("seed", n);           // per sorted position, +inf to start
+    k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>((uint32_t *)seed, n, 0x7f800000u); ++launches;
     uint32_t *lkey = sc.get<uint32_t>("lkey", n), *lkey2 = sc.get<uint32_t>("lkey2", n);
     k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n); ++launches;
     int64_t m = n;
@@ -468,8 +468,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
 
     // per-level cell hash maps, built on first use
     struct LevelTab {
-        uint64_t *hkey = nullptr;
-        uint2 *hval = nullptr;
+        uint4 *slot = nullptr;
         uint32_t mask = 0;
         bool built = false;
     };
@@ -483,11 +482,10 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         uint32_t ncells = read1(small + 0);
         uint32_t H = 1;
         while (H < 2 * ncells) H <<= 1;
-        uint64_t *hkey = sc.get<uint64_t>("hkey" + std::to_string(L), H);
-        uint2 *hval = sc.get<uint2>("hval" + std::to_string(L), H);
-        CK(cudaMemsetAsync(hkey, 0xff, sizeof(uint64_t) * H, s));
-        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, hkey, hval, H - 1); ++launches;
-        tabs[L] = {hkey, hval, H - 1, true};
+        uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
+        CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
+        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
+        tabs[L] = {slot, H - 1, true};
     };
 
     // work items of a (level, position)-ordered list of sorted positions
@@ -531,6 +529,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     };
 
     int pass = 0;
+    int64_t cand_before = 0;
     int first_level = -1;
     while (m > 0) {
         if (pass > 4 * MAX_LEVELS) fail(KNN_ERR_CUDA, "internal: too many passes");
@@ -557,11 +556,11 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.keys = keys;
         a.counter = small + 3;
         for (int L = 0; L < MAX_LEVELS; ++L) {
-            a.hkeyL[L] = tabs[L].hkey;
-            a.hvalL[L] = tabs[L].hval;
+            a.hslotL[L] = tabs[L].slot;
             a.hmaskL[L] = tabs[L].mask;
         }
         a.fail = status;
+        a.seed = seed;
         a.out_ids = ids;
         a.out_dist = dist;
         a.stats = st;
@@ -593,6 +592,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
             ms_scan += t;
+            if (pass < 16) stats.ms_pass[pass] = t;
+            CK(cudaMemcpyAsync(pinned + 8, st, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            unsigned long long c;
+            memcpy(&c, pinned + 8, sizeof(c));
+            if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
+            cand_before = (int64_t)c;
         }
         if (fast) {
             // queries whose buffer overflowed (massive ties): general kernel
@@ -708,7 +714,7 @@ static size_t job_footprint(const knnjoin_job &j)
     const size_t n = (size_t)std::max<int64_t>(j.n, 0);
     size_t H = 1;
     while (H < 2 * n) H <<= 1;
-    size_t b = n * (size_t)(4 * j.d + 4 * pad_dim(std::max(1, std::min(j.d, MAX_DIM))) + 24 + 72) + 2 * H * 16;
+    size_t b = n * (size_t)(4 * j.d + 4 * pad_dim(std::max(1, std::min(j.d, MAX_DIM))) + 24 + 76) + 2 * H * 16;
     if (!is_device_ptr(j.points)) b += n * (size_t)j.d * 4;
     if (!is_device_ptr(j.out_ids)) b += n * (size_t)j.K * 4;
     if (!is_device_ptr(j.out_dist)) b += n * (size_t)j.K * 8;
@@ -813,9 +819,9 @@ static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f)
 // Diagnostics build only: read (and optionally clear) the phase counters.
 extern "C" int knnjoin_debug_phases(unsigned long long *out, int reset)
 {
-    if (cudaMemcpyFromSymbol(out, knn::g_phase, sizeof(unsigned long long) * 8) != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(out, knn::g_phase, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
     if (reset) {
-        unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned long long z[16] = {};
         if (cudaMemcpyToSymbol(knn::g_phase, z, sizeof(z)) != cudaSuccess) return 1;
     }
     return 0;

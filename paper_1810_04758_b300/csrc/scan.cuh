@@ -43,10 +43,10 @@ struct ScanArgs {
     const uint2 *items;        // (first active index, count | level << 16)
     uint32_t nitems;
     uint32_t *counter;         // work-queue head
-    const uint64_t *hkeyL[MAX_LEVELS];  // per-level hash maps (cell key -> run)
-    const uint2 *hvalL[MAX_LEVELS];
+    const uint4 *hslotL[MAX_LEVELS];    // per-level hash maps (cell key -> run)
     uint32_t hmaskL[MAX_LEVELS];
     uint32_t *fail;            // [n] per sorted position: 0 certified, 1 not, 2 overflow
+    float *seed;               // [n] per sorted position: FP32-filter threshold carried to the next pass
     int32_t *out_ids;          // [n][K]
     double *out_dist;          // [n][K]
     unsigned long long *stats; // [0] candidates, [1] overflow rounds, [2] band entries
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 ok = ok && nb[k] >= 0 && nb[k] <= cmaxL[k];
             }
             uint2 rg = make_uint2(0, 0);
-            if (ok) rg = hash_lookup(a.hkeyL[level], a.hvalL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
+            if (ok) rg = hash_lookup(a.hslotL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
             nb_range[t] = rg;
         }
         __syncthreads();

@@ -35,7 +35,10 @@ namespace knn {
 // warp adds clock64() deltas per phase of k_scan2 to g_phase; otherwise the
 // markers compile to nothing.
 #ifdef KNN_PHASE_TIMING
-__device__ unsigned long long g_phase[8];
+// [0, 8) cycles per phase; per item: [8] max cycles, [9] sum, [10] count,
+// [11] max query-tiles, [12] sum of Q, [13] max cycles / [14] sum / [15]
+// count of items with Q <= 2
+__device__ unsigned long long g_phase[16];
 #define KNN_PT_DECL unsigned long long ph_[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pt_ = clock64()
 #define KNN_PT(i)                                          \
     do {                                                   \
@@ -48,6 +51,24 @@ __device__ unsigned long long g_phase[8];
         if ((threadIdx.x & 31) == 0)                       \
             for (int q_ = 0; q_ < 8; ++q_) atomicAdd(&g_phase[q_], ph_[q_]); \
     } while (0)
+#define KNN_ITEM_BEGIN unsigned long long it0_ = clock64(), itq_ = 0
+#define KNN_ITEM_TILE(x) itq_ += (x)
+#define KNN_ITEM_END(Q)                                                    \
+    do {                                                                   \
+        if ((threadIdx.x & 31) == 0) {                                     \
+            const unsigned long long dt_ = clock64() - it0_;               \
+            atomicMax(&g_phase[8], dt_);                                   \
+            atomicAdd(&g_phase[9], dt_);                                   \
+            atomicAdd(&g_phase[10], 1ull);                                 \
+            atomicMax(&g_phase[11], itq_);                                 \
+            atomicAdd(&g_phase[12], (unsigned long long)(Q));              \
+            if ((Q) <= 2) {                                                \
+                atomicMax(&g_phase[13], dt_);                              \
+                atomicAdd(&g_phase[14], dt_);                              \
+                atomicAdd(&g_phase[15], 1ull);                             \
+            }                                                              \
+        }                                                                  \
+    } while (0)
 #else
 #define KNN_PT_DECL
 #define KNN_PT(i) \
@@ -56,15 +77,39 @@ __device__ unsigned long long g_phase[8];
 #define KNN_PT_FLUSH \
     do {             \
     } while (0)
+#define KNN_ITEM_BEGIN
+#define KNN_ITEM_TILE(x) \
+    do {                 \
+    } while (0)
+#define KNN_ITEM_END(Q) \
+    do {                \
+    } while (0)
 #endif
 
 constexpr int S2_WARPS = 4;
 
+// Runs of at least S2_BIG points are scanned in super-tiles of S2_SUPER
+// consecutive points, each skipped by the queries it cannot serve.
+#ifndef S2_BIG
+#define S2_BIG 256
+#endif
+#ifndef S2_SUPER
+#define S2_SUPER 128
+#endif
+
+// Start-threshold prefilter of a pass, in units of the squared certificate
+// radius (0: none).
+#ifndef KNN_PREFILTER_R2
+#define KNN_PREFILTER_R2 1.0f
+#endif
+
 // Neighbour offsets of the 3^d box, nearest first: for each d the offset
 // codes (base-3 digits, digit 1 = no move) ordered by how many dimensions
-// move (0, then faces, edges, ...).  Filled once per device by the host.
+// move (0, then faces, edges, ...).  Filled once per device by the host; read
+// through the read-only data cache (lanes read different entries, which the
+// constant cache would serialise).
 constexpr int NB_ORDER_TOTAL = 3 + 9 + 27 + 81 + 243 + 729 + 2187 + 6561;
-__constant__ uint16_t c_nb_order[NB_ORDER_TOTAL];
+__device__ uint16_t g_nb_order[NB_ORDER_TOTAL];
 __host__ __device__ constexpr int nb_order_offset(int d)
 {
     return d <= 1 ? 0 : nb_order_offset(d - 1) + (d == 2 ? 3 : d == 3 ? 9 : d == 4 ? 27 : d == 5 ? 81 : d == 6 ? 243 : d == 7 ? 729 : 2187);
@@ -252,6 +297,21 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&V)[E], int lane)
 // position (as float bits), padded to a multiple of 4 floats (vector loads).
 __host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) & ~3; }
 
+// Entries of the per-item table of neighbour key parts (even, so that what
+// follows stays 16-byte aligned).
+__host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; }
+
+// Bytes of one warp's shared memory in k_scan2 (16-byte multiple):
+// candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
+// [QM][QP] f32, counts and sorted positions [QM] x 2, radix histogram [256],
+// squared face gaps [QM][3d] f32, the item's cell and the level's extent
+// [2d] i32.
+__host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
+{
+    return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
+            (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)2 * d * 4 + 15) & ~(size_t)15;
+}
+
 template <int DIM>
 __device__ __forceinline__ void load_query_row(const float *qc, int i, float (&q)[DIM], float &thr, uint32_t &qs)
 {
@@ -362,6 +422,127 @@ __device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, uint32_t
     return make_int2(c1, __float_as_int(nt));
 }
 
+// Append this tile's accepted candidates (ballot `bal`) to query i's buffer;
+// on overflow shrink it to the band of its K-th value first, and mark the
+// query for the general kernel (count -1, threshold -1) if even that does
+// not make room.  The count of query i lives in lane i's `my_cnt`.
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int i,
+                                             bool acc, uint32_t bal, float d2, uint32_t s, int K, float ti,
+                                             int lane)
+{
+    constexpr int B = 32 * E;
+    constexpr int QP = query_row_floats(DIM);
+    uint64_t *bi = buf + i * B;
+    int c0 = __shfl_sync(FULL, my_cnt, i);
+    int nnew = __popc(bal);
+    if (c0 + nnew > B) {
+        // buffer full: drop to the K-th value's band (rare)
+        int2 r2 = shrink_buffer(bi, c0, K, hist, lane, ti);
+        c0 = r2.x;
+        const float nt = __int_as_float(r2.y);
+        acc = acc && d2 <= nt;
+        bal = __ballot_sync(FULL, acc);
+        nnew = __popc(bal);
+        float tnew = nt;
+        if (c0 + nnew > B) {  // too many ties: general kernel
+            c0 = -1;
+            tnew = -1.0f;
+            acc = false;
+            nnew = 0;
+        }
+        if (lane == 0) qc[i * QP + DIM] = tnew;
+        __syncwarp();
+    }
+    if (acc) bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
+    if (lane == i) my_cnt = c0 < 0 ? -1 : c0 + nnew;
+}
+
+// Queries (bit i = query i) that points [sb, se) of the sorted order can
+// serve.  Those keys share their bits above the highest bit in which the
+// first and last differ, so the points lie in the box of that key prefix:
+// in dimension k the level-0 cells whose low fb_k bits are free, fb_k = the
+// number of key bits of dimension k below that bit.  A query is dropped when
+// the rounded-down squared distance to the box exceeds its threshold (with
+// the 2^-19 margin of the cell test).
+template <int DIM>
+__device__ __forceinline__ uint32_t super_tile_mask(const ScanArgs &a, uint32_t sb, uint32_t se, const float *qc,
+                                                    int Q, int lane)
+{
+    constexpr int QP = query_row_floats(DIM);
+    const uint64_t k0 = a.keys[sb], k1 = a.keys[se - 1];
+    const uint64_t x = k0 ^ k1;
+    const int hb = x ? 64 - __clzll((long long)x) : 0;  // free low key bits
+    float blo = 0.0f, bhi = 0.0f;
+    if (lane < DIM) {
+        const int fb = hb > lane ? (hb - lane + DIM - 1) / DIM : 0;
+        if (fb >= 30) {
+            blo = -__int_as_float(0x7f800000);
+            bhi = __int_as_float(0x7f800000);
+        } else {
+            int cc = 0;
+            for (int b = fb; b < a.bits; ++b) cc |= (int)((k0 >> (b * DIM + lane)) & 1u) << b;
+            blo = face_of(cc, a.lo[lane], a.w0);
+            bhi = face_of(cc + (1 << fb), a.lo[lane], a.w0);
+        }
+    }
+    float lb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float lo = __shfl_sync(FULL, blo, k), hi = __shfl_sync(FULL, bhi, k);
+        if (lane < Q) {
+            const float q = qc[lane * QP + k];
+            const float g = fmaxf(fmaxf(__fsub_rd(lo, q), __fsub_rd(q, hi)), 0.0f);
+            lb = __fadd_rd(lb, __fmul_rd(g, g));
+        }
+    }
+    const bool keep = lane < Q && !(lb > qc[lane * QP + DIM] * (1.0f + 0x1p-19f));
+    return __ballot_sync(FULL, keep);
+}
+
+// Score one tile (lane = candidate s with coordinates c, `valid` lanes only)
+// against the queries in `tmask` and append the accepted ones to their buffers.
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bool valid, uint32_t tmask,
+                                           uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K, int lane)
+{
+    // the queries this tile can serve; for d >= 5, two at a time
+    // (independent dependency chains: a query's threshold only
+    // changes in its own insert, so both use current thresholds)
+    if (DIM >= 5) {
+        for (uint32_t m = tmask; m;) {
+            const int i0 = __ffs(m) - 1;
+            m &= m - 1;
+            const int i1 = m ? __ffs(m) - 1 : i0;
+            const bool two = m != 0;
+            m &= m - 1;
+            float q0[DIM], q1[DIM], t0v, t1v;
+            uint32_t s0, s1;
+            load_query_row<DIM>(qc, i0, q0, t0v, s0);
+            load_query_row<DIM>(qc, i1, q1, t1v, s1);
+            const float d0 = dist2_f32<DIM>(q0, c);
+            const float d1 = dist2_f32<DIM>(q1, c);
+            const bool acc0 = valid && d0 <= t0v && s != s0;
+            const bool acc1 = two && valid && d1 <= t1v && s != s1;
+            const uint32_t bal0 = __ballot_sync(FULL, acc0);
+            const uint32_t bal1 = __ballot_sync(FULL, acc1);
+            if (bal0) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i0, acc0, bal0, d0, s, K, t0v, lane);
+            if (bal1) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i1, acc1, bal1, d1, s, K, t1v, lane);
+        }
+    } else {
+        for (uint32_t m = tmask; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            float qv[DIM], ti;
+            uint32_t qi_s;
+            load_query_row<DIM>(qc, i, qv, ti, qi_s);
+            const float d2 = dist2_f32<DIM>(qv, c);
+            const bool acc = valid && d2 <= ti && s != qi_s;
+            const uint32_t bal = __ballot_sync(FULL, acc);
+            if (bal) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, acc, bal, d2, s, K, ti, lane);
+        }
+    }
+}
+
 template <int DIM, int QM, int E>
 __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
 {
@@ -374,15 +555,19 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
 
     // per-warp shared memory
     constexpr int BS = B;
-    const size_t wbytes = (size_t)QM * BS * 8 + (size_t)QM * QP * 4 + (size_t)QM * 8 + 256 * 4 +
-                          (size_t)QM * 2 * DIM * 4;
-    unsigned char *wb = smem + warp * ((wbytes + 15) & ~(size_t)15);
+    constexpr int GQ = 3 * DIM;  // squared-gap row of a query
+    unsigned char *wb = smem + warp * scan2_warp_bytes(DIM, QM, E);
     uint64_t *buf = (uint64_t *)wb;            // [QM][BS]  (d2_32 bits << 32 | sorted index)
-    float *qc = (float *)(buf + QM * BS);      // [QM][QP] coords, threshold, sorted position
+    uint64_t *dil = buf + QM * BS;             // [3d] Morton bits of neighbour coordinates
+    float *qc = (float *)(dil + dil_entries(DIM));  // [QM][QP] coords, threshold, sorted position
     int *cnt = (int *)(qc + QM * QP);          // [QM]
     uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
     uint32_t *hist = qsv + QM;                 // [256]
-    float *gaps = (float *)(hist + 256);       // [QM][2*DIM] distance to own cell's faces (rounded down)
+    // [QM][3d]: per dimension, the squared distance (rounded down) from the
+    // query to the lower neighbour cell, 0 (same slab), to the upper one --
+    // indexed by the base-3 digit of a neighbour offset
+    float *gsq = (float *)(hist + 256);
+    int *cellv = (int *)(gsq + QM * GQ);       // [2d]
 
     unsigned long long st_cand = 0, st_band = 0;
     KNN_PT_DECL;
@@ -392,16 +577,13 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
         if (lane == 0) item = atomicAdd(a.counter, 1u);
         item = __shfl_sync(FULL, item, 0);
         if (item >= a.nitems) break;
+        KNN_ITEM_BEGIN;
         const uint2 it = a.items[item];
         const int Q = (int)(it.y & 0xffffu);
         const int level = (int)(it.y >> 16);
         const int shift = DIM * level;
         const int nbits = a.bits - level;
-        int cmaxL[DIM];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) cmaxL[k] = a.cmax0[k] >> level;
-        const uint64_t *hkey = a.hkeyL[level];
-        const uint2 *hval = a.hvalL[level];
+        const uint4 *hslot = a.hslotL[level];
         const uint32_t hmask = a.hmaskL[level];
 
         if (lane < Q) {
@@ -413,8 +595,40 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
             for (int k = 0; k < DIM; ++k) qc[lane * QP + k] = c[k];
         }
         __syncwarp();
-        int cell[DIM];
-        morton_decode(a.keys[qsv[0]] >> shift, DIM, nbits, cell);
+        // the item's cell at its level and the level's last cell index, kept
+        // in shared memory (cellv) rather than registers across the scan
+        {
+            int cell[DIM];
+            morton_decode(a.keys[qsv[0]] >> shift, DIM, nbits, cell);
+            if (lane < DIM) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k)
+                    if (k == lane) {
+                        cellv[k] = cell[k];
+                        cellv[DIM + k] = a.cmax0[k] >> level;
+                    }
+            }
+        }
+        __syncwarp();
+        const int *cell = cellv, *cmaxL = cellv + DIM;
+        // neighbour keys by parts: dil[3k + g] holds the level-key bits of
+        // coordinate k of the neighbour at digit g (cell[k] + g - 1), so a
+        // neighbour's key is the OR of d table entries; bit 3k + g of nbad
+        // marks a coordinate outside the level's grid
+        uint32_t nbad;
+        {
+            bool bad = false;
+            if (lane < 3 * DIM) {
+                const int k = lane / 3;
+                const int c = cell[k] + lane % 3 - 1;
+                bad = c < 0 || c > cmaxL[k];
+                uint64_t v = 0;
+                for (int b = 0; b < nbits; ++b) v |= (uint64_t)((c >> b) & 1) << (b * DIM + k);
+                dil[lane] = v;
+            }
+            nbad = __ballot_sync(FULL, bad);
+        }
+        __syncwarp();
         // query state: threshold and sorted position sit in the query's row
         // (one broadcast vector load gives a pair everything it needs); the
         // buffer count lives in lane i's register for query i
@@ -423,14 +637,24 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
             float q[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
-            const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                gaps[lane * 2 * DIM + 2 * k] = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
-                gaps[lane * 2 * DIM + 2 * k + 1] = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
+                // q lies in [face(c), face(c+1)) exactly, so both gaps are >= 0
+                const float gl = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
+                const float gh = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
+                gsq[lane * GQ + 3 * k] = __fmul_rd(gl, gl);
+                gsq[lane * GQ + 3 * k + 1] = 0.0f;
+                gsq[lane * GQ + 3 * k + 2] = __fmul_rd(gh, gh);
             }
-            qc[lane * QP + DIM] = isinf(R) ? __int_as_float(0x7f800000)
-                                           : __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-14f);
+            // start threshold: the certificate prefilter KNN_PREFILTER_R2 x R^2
+            // (points beyond R cannot be in a certified answer), or the band
+            // of the K-th value an earlier pass found in a smaller box
+            // (contained in this one), whichever is lower
+            const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
+            const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
+                                   ? __int_as_float(0x7f800000)
+                                   : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
+            qc[lane * QP + DIM] = fminf(thr0, a.seed[qsv[lane]]);
             qc[lane * QP + DIM + 1] = __uint_as_float(qsv[lane]);
         }
         __syncwarp();
@@ -440,20 +664,22 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
         for (int ob = 0; ob < NOFF; ob += 32) {
             const int o = ob + lane;
             uint32_t rb = 0, re = 0;
-            int code = 0;
+            int goff[DIM];  // offset of this cell's squared gap, per dimension
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) goff[k] = 3 * k + 1;
             if (o < NOFF) {
-                int nb[DIM];
-                int r = c_nb_order[nb_order_offset(DIM) + o];
-                code = r;
-                bool ok = true;
+                int r = __ldg(&g_nb_order[nb_order_offset(DIM) + o]);
+                uint64_t key = 0;
+                uint32_t hit = 0;
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
-                    nb[k] = cell[k] + (r % 3) - 1;
+                    goff[k] = 3 * k + r % 3;
                     r /= 3;
-                    ok = ok && nb[k] >= 0 && nb[k] <= cmaxL[k];
+                    key |= dil[goff[k]];
+                    hit |= nbad >> goff[k];
                 }
-                if (ok) {
-                    uint2 rg = hash_lookup(hkey, hval, hmask, morton_encode(nb, DIM, nbits));
+                if (!(hit & 1u)) {
+                    const uint2 rg = hash_lookup(hslot, hmask, key);
                     rb = rg.x;
                     re = rg.y;
                 }
@@ -465,27 +691,58 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
             uint32_t cmask = 0;
             if (len) {
                 for (int i = 0; i < Q; ++i) {
-                    float lb = 0.0f;
-                    int r = code;
+                    const float *g = gsq + i * GQ;
+                    float lb = g[goff[0]];
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) {
-                        const int dg = r % 3;
-                        r /= 3;
-                        if (dg != 1) {
-                            const float g = gaps[i * 2 * DIM + 2 * k + (dg == 2 ? 1 : 0)];
-                            lb = __fmaf_rd(g, g, lb);
-                        }
-                    }
+                    for (int k = 1; k < DIM; ++k) lb = __fadd_rd(lb, g[goff[k]]);
                     if (!(lb > qc[i * QP + DIM] * (1.0f + 0x1p-19f))) cmask |= 1u << i;
                 }
             }
-            uint32_t inc = len;
+            // long runs first, outside the flattened scan
+            const bool bigcell = len >= S2_BIG;
+            const uint32_t bigmask = __ballot_sync(FULL, bigcell && cmask != 0);
+            // long runs: super-tiles, starting at the one that holds the
+            // item's first query when it lies in the run (nearby in key order
+            // is mostly nearby in space) and alternating outwards
+            for (uint32_t bm = bigmask; bm; bm &= bm - 1) {
+                const int src = __ffs(bm) - 1;
+                const uint32_t cb = __shfl_sync(FULL, rb, src), ce = __shfl_sync(FULL, re, src);
+                const uint32_t cmk = __shfl_sync(FULL, cmask, src);
+                const int nst = (int)((ce - cb + S2_SUPER - 1) / S2_SUPER);
+                const uint32_t sq = qsv[0];
+                const int u0 = (sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
+                for (int j = 0, left = nst; left > 0; ++j) {
+                    const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
+                    if (u < 0 || u >= nst) continue;
+                    --left;
+                    const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
+                    const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
+                    const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                    if (!smask) continue;
+                    for (uint32_t t0 = sb; t0 < se; t0 += 32) {
+                        const bool valid = t0 + lane < se;
+                        const uint32_t s = valid ? t0 + lane : 0u;
+                        float c[DIM];
+                        if (valid) {
+                            load_point<DIM>(a.xsort, s, c);
+                            st_cand += (unsigned long long)__popc(smask);
+                            KNN_ITEM_TILE(__popc(smask));
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                        }
+                        scan2_tile<DIM, E>(c, s, valid, smask, buf, qc, hist, my_cnt, K, lane);
+                    }
+                }
+            }
+            const uint32_t flen = bigcell ? 0u : len;
+            uint32_t inc = flen;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 uint32_t y = __shfl_up_sync(FULL, inc, d);
                 if (lane >= d) inc += y;
             }
-            const uint32_t exc = inc - len;
+            const uint32_t exc = inc - flen;
             const uint32_t total = __shfl_sync(FULL, inc, 31);
             KNN_PT(1);
             for (uint32_t t0 = 0; t0 < total; t0 += 32) {
@@ -505,46 +762,13 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                 float c[DIM];
                 if (valid) {
                     load_point<DIM>(a.xsort, s, c);
-                    st_cand += (unsigned long long)Q;
+                    st_cand += (unsigned long long)__popc(tmask);  // distances evaluated
+                    KNN_ITEM_TILE(__popc(tmask));
                 } else {
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
                 }
-#pragma unroll 2
-                for (int i = 0; i < Q; ++i) {
-                    if (!((tmask >> i) & 1u)) continue;
-                    float qv[DIM], ti;
-                    uint32_t qi_s;
-                    load_query_row<DIM>(qc, i, qv, ti, qi_s);
-                    const float d2 = dist2_f32<DIM>(qv, c);
-                    bool acc = valid && d2 <= ti && s != qi_s;
-                    uint32_t bal = __ballot_sync(FULL, acc);
-                    if (bal) {
-                        uint64_t *bi = buf + i * BS;
-                        int c0 = __shfl_sync(FULL, my_cnt, i);
-                        int nnew = __popc(bal);
-                        if (c0 + nnew > B) {
-                            // buffer full: drop to the K-th value's band (rare)
-                            int2 r2 = shrink_buffer(bi, c0, K, hist, lane, ti);
-                            c0 = r2.x;
-                            const float nt = __int_as_float(r2.y);
-                            acc = acc && d2 <= nt;
-                            bal = __ballot_sync(FULL, acc);
-                            nnew = __popc(bal);
-                            float tnew = nt;
-                            if (c0 + nnew > B) {  // too many ties: general kernel
-                                c0 = -1;
-                                tnew = -1.0f;
-                                acc = false;
-                                nnew = 0;
-                            }
-                            if (lane == 0) qc[i * QP + DIM] = tnew;
-                            __syncwarp();
-                        }
-                        if (acc) bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
-                        if (lane == i) my_cnt = c0 < 0 ? -1 : c0 + nnew;
-                    }
-                }
+                scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane);
             }
             KNN_PT(2);
         }
@@ -644,6 +868,8 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
                     certified = dk < f32_to_f64_bits_floor(R2);
                 }
                 KNN_PT(6);
+                // not certified: the K-th value bounds the next pass's threshold
+                if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
                 if (certified) {
                     flag = 0;
                     const int64_t row = (int64_t)a.perm[qsv[i]] * K;
@@ -661,6 +887,7 @@ __global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
             KNN_PT(7);
         }
         __syncwarp();
+        KNN_ITEM_END(Q);
     }
     KNN_PT_FLUSH;
     for (int o = 16; o; o >>= 1) {

@@ -58,7 +58,8 @@ def test_struct_layouts_match_header(tmp_path):
                                kj.KnnjoinConfig.hbm_budget_bytes.offset, kj.KnnjoinConfig.workers.offset]
     assert lines["job"] == [ctypes.sizeof(kj.KnnjoinJob), kj.KnnjoinJob.out_dist.offset]
     assert lines["stats"] == [ctypes.sizeof(kj.KnnjoinStats), kj.KnnjoinStats.candidates.offset,
-                              kj.KnnjoinStats.ms_index.offset, kj.KnnjoinStats.ms_wall.offset]
+                              kj.KnnjoinStats.ms_index.offset, kj.KnnjoinStats.ms_wall.offset,
+                              kj.KnnjoinStats.ms_pass.offset, kj.KnnjoinStats.pass_candidates.offset]
 
 
 def test_exact_arithmetic_matches_ieee_double_on_host(tmp_path):
