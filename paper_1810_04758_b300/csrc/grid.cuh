@@ -112,28 +112,56 @@ __global__ void k_eps_pairs(const float *xs, int64_t n, int d, int64_t sm, PrepR
     }
 }
 
-// Histogram of distances from S sample points (stride n / S) to m subset
-// points (stride n / m), bins of width range / 1024 over [0, range), where
-// range = eps_mean (stage 0) or twice the stage-0 estimate (stage 1).
-__global__ void k_eps_hist(const float *xs, int64_t n, int d, int64_t S, int64_t m,
-                           const GridParams *gp, PrepReduce *red, int stage)
+// Rows of the S sample points (stride n / S) and of the m subset points
+// (stride n / m), 8 floats each (zero padded), for the sampled-distance
+// kernels below.
+__global__ void k_eps_rows(const float *__restrict__ xs, int64_t n, int d, int64_t S, int64_t m,
+                           float *__restrict__ srow, float *__restrict__ mrow)
+{
+    const int64_t sstride = n / S, mstride = n / m;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < S + m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const bool smp = t < S;
+        const int64_t i = smp ? t * sstride : (t - S) * mstride;
+        float *row = smp ? srow + t * 8 : mrow + (t - S) * 8;
+        for (int k = 0; k < 8; ++k) row[k] = k < d ? xs[(int64_t)k * n + i] : 0.0f;
+    }
+}
+
+__device__ __forceinline__ float row_dist(const float *a, const float *b, int d)
+{
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        const float t = a[k] - b[k];
+        s = fmaf(t, t, s);
+    }
+    return sqrtf(s);
+}
+
+// Histogram of distances from the S sample points to the m subset points,
+// bins of width range / 1024 over [0, range), where range = eps_mean (stage
+// 0) or twice the stage-0 estimate (stage 1).  A thread holds one subset
+// point and walks the samples (staged in shared memory).
+__global__ void k_eps_hist(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n, int d,
+                           int64_t S, int64_t m, const GridParams *gp, PrepReduce *red, int stage)
 {
     __shared__ unsigned h[1024];
+    __shared__ float sp[256 * 8];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
+    for (int i = threadIdx.x; i < (int)S * 8; i += blockDim.x) sp[i] = srow[i];
     __syncthreads();
-    float range = stage == 0 ? gp->eps_mean : 2.0f * gp->eps_min;
+    const float range = stage == 0 ? gp->eps_mean : 2.0f * gp->eps_min;
     if (range > 0.0f) {
-        float inv_bw = 1024.0f / range;
-        int64_t sstride = n / S, mstride = n / m;
-        int64_t total = S * m;
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-             t += (int64_t)gridDim.x * blockDim.x) {
-            int64_t si = (t / m) * sstride, mj = (t % m) * mstride;
-            if (si == mj) continue;
-            float dd = dist_f32(xs, n, d, si, mj);
-            if (dd < range) {
-                int b = min((int)(dd * inv_bw), 1023);
-                atomicAdd(&h[b], 1u);
+        const float inv_bw = 1024.0f / range;
+        const int64_t sstride = n / S, mstride = n / m;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            float p[8];
+            for (int k = 0; k < 8; ++k) p[k] = mrow[j * 8 + k];
+            for (int64_t i = 0; i < S; ++i) {
+                if (i * sstride == j * mstride) continue;
+                const float dd = row_dist(sp + i * 8, p, d);
+                if (dd < range) atomicAdd(&h[min((int)(dd * inv_bw), 1023)], 1u);
             }
         }
     }
@@ -153,23 +181,37 @@ struct ParamsIn {
 
 // Density skew: neighbours of each sampled point among the subset within
 // the radius where about K are expected (eps_min scaled by (n/m)^(1/d)).
-__global__ void k_eps_count(const float *xs, int64_t n, int d, int64_t S, int64_t m,
-                            const GridParams *gp, PrepReduce *red)
+// A thread holds one subset point; per sample, a warp ballot counts its
+// lanes within the radius.
+__global__ void k_eps_count(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n, int d,
+                            int64_t S, int64_t m, const GridParams *gp, PrepReduce *red)
 {
-    // radius at which a sample expects about K neighbours within the subset
+    __shared__ unsigned cnt[256];
+    __shared__ float sp[256 * 8];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    for (int i = threadIdx.x; i < (int)S * 8; i += blockDim.x) sp[i] = srow[i];
+    __syncthreads();
     const float e = gp->eps_min * powf((float)n / (float)m, 1.0f / (float)d);
-    if (!(e > 0.0f) || !isfinite(e)) return;
-    int64_t sstride = n / S, mstride = n / m;
-    for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
-        unsigned c = 0;
-        int64_t si = s * sstride;
-        for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
-            int64_t mj = t * mstride;
-            if (mj != si && dist_f32(xs, n, d, si, mj) < e) ++c;
+    if (e > 0.0f && isfinite(e)) {
+        const int64_t sstride = n / S, mstride = n / m;
+        // every lane of a warp runs the same number of rounds (ballots)
+        const int64_t span = (int64_t)gridDim.x * blockDim.x;
+        const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+        for (int64_t base = first; base < m; base += span) {
+            const int64_t j = base + (threadIdx.x & 31);
+            const bool valid = j < m;
+            float p[8];
+            for (int k = 0; k < 8; ++k) p[k] = valid ? mrow[j * 8 + k] : 0.0f;
+            for (int64_t i = 0; i < S; ++i) {
+                const bool in = valid && i * sstride != j * mstride && row_dist(sp + i * 8, p, d) < e;
+                const unsigned b = __ballot_sync(FULL, in);
+                if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt[i], (unsigned)__popc(b));
+            }
         }
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&red->scount[s], c);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)S; i += blockDim.x)
+        if (cnt[i]) atomicAdd(&red->scount[i], cnt[i]);
 }
 
 __device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in);

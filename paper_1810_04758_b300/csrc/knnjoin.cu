@@ -1,7 +1,8 @@
 // knnjoin.cu -- host orchestration and the C ABI (include/knnjoin.h).
 //
 // A join runs on one CUDA stream:
-//   a1 k_prep -> a2 k_eps_pairs, k_eps_hist x2, k_params x3 -> a3 k_keys ->
+//   a1 k_prep -> a2 k_eps_pairs, k_eps_rows, k_eps_hist x2, k_eps_count,
+//   k_params x4 -> a3 k_keys ->
 //   a4 radix sort -> a5 k_gather -> pass loop { level cells + hash map,
 //   groups of the active queries, density order, work items, a7-a11 k_scan,
 //   compaction of the uncertified queries } until no query is left.
@@ -393,12 +394,16 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     pin.width_mult = width_mult;
     pin.start_level = 0;
     pin.max_finer = 3;
+    float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
+    float *mrow = sc.get<float>("eps_mrow", (size_t)pin.m * 8);
+    k_eps_rows<<<grid_for(pin.S + pin.m, 256, nsm), 256, 0, s>>>(xs, n, d, pin.S, pin.m, srow, mrow); ++launches;
+    const unsigned gm = (unsigned)((pin.m + 255) / 256);
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
-    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 0); ++launches;
+    k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 0); ++launches;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
-    k_eps_hist<<<grid_for(pin.S * pin.m, 256, nsm, 4), 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red, 1); ++launches;
+    k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 1); ++launches;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
-    k_eps_count<<<(unsigned)pin.S, 256, 0, s>>>(xs, n, d, pin.S, pin.m, gp, red); ++launches;
+    k_eps_count<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red); ++launches;
     k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
     CK(cudaGetLastError());
     GridParams hp = read1(gp);
@@ -715,6 +720,7 @@ static size_t job_footprint(const knnjoin_job &j)
     size_t H = 1;
     while (H < 2 * n) H <<= 1;
     size_t b = n * (size_t)(4 * j.d + 4 * pad_dim(std::max(1, std::min(j.d, MAX_DIM))) + 24 + 76) + 2 * H * 16;
+    b += 32 * std::min<size_t>(n, 65536) + 8192;  // sampled-distance rows
     if (!is_device_ptr(j.points)) b += n * (size_t)j.d * 4;
     if (!is_device_ptr(j.out_ids)) b += n * (size_t)j.K * 4;
     if (!is_device_ptr(j.out_dist)) b += n * (size_t)j.K * 8;

@@ -97,6 +97,11 @@ constexpr int S2_WARPS = 4;
 #define S2_SUPER 128
 #endif
 
+// Resident CTAs per SM the register allocation is sized for.
+#ifndef S2_MIN_CTAS
+#define S2_MIN_CTAS 5
+#endif
+
 // Start-threshold prefilter of a pass, in units of the squared certificate
 // radius (0: none).
 #ifndef KNN_PREFILTER_R2
@@ -544,7 +549,7 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
 }
 
 template <int DIM, int QM, int E>
-__global__ void __launch_bounds__(S2_CTA, 5) k_scan2(ScanArgs a)
+__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = pad_dim(DIM);
