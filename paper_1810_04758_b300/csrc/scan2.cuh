@@ -97,6 +97,16 @@ constexpr int S2_WARPS = 4;
 #define S2_SUPER 128
 #endif
 
+// Smallest d whose tiles score two queries at a time.
+#ifndef S2_PAIR_DIM
+#define S2_PAIR_DIM 5
+#endif
+
+// Smallest d scanned two tiles (64 candidates) at a time.
+#ifndef S2_WIDE_DIM
+#define S2_WIDE_DIM 2
+#endif
+
 // Resident CTAs per SM the register allocation is sized for.
 #ifndef S2_MIN_CTAS
 #define S2_MIN_CTAS 5
@@ -511,10 +521,10 @@ template <int DIM, int E>
 __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bool valid, uint32_t tmask,
                                            uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K, int lane)
 {
-    // the queries this tile can serve; for d >= 5, two at a time
+    // the queries this tile can serve; for d >= S2_PAIR_DIM, two at a time
     // (independent dependency chains: a query's threshold only
     // changes in its own insert, so both use current thresholds)
-    if (DIM >= 5) {
+    if (DIM >= S2_PAIR_DIM) {
         for (uint32_t m = tmask; m;) {
             const int i0 = __ffs(m) - 1;
             m &= m - 1;
@@ -545,6 +555,33 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
             const uint32_t bal = __ballot_sync(FULL, acc);
             if (bal) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, acc, bal, d2, s, K, ti, lane);
         }
+    }
+}
+
+// Two tiles at once (lane = candidates sA and sB, NaN coordinates past the
+// end of the list): each query's row is read
+// once for 64 candidates and its two distances are independent chains.  The
+// second batch may be tested against a threshold the first batch's insert
+// has since lowered; that only keeps extra entries (the buffer holds a
+// superset of what its threshold admits).
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const float (&cB)[DIM], uint32_t sA,
+                                                uint32_t sB, uint32_t tmask, uint64_t *buf,
+                                                float *qc, uint32_t *hist, int &my_cnt, int K, int lane)
+{
+    for (uint32_t m = tmask; m; m &= m - 1) {
+        const int i = __ffs(m) - 1;
+        float qv[DIM], ti;
+        uint32_t qi_s;
+        load_query_row<DIM>(qc, i, qv, ti, qi_s);
+        const float dA = dist2_f32<DIM>(qv, cA);
+        const float dB = dist2_f32<DIM>(qv, cB);
+        const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
+        const bool accB = dB <= ti && sB != qi_s;
+        const uint32_t balA = __ballot_sync(FULL, accA);
+        const uint32_t balB = __ballot_sync(FULL, accB);
+        if (balA) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
+        if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB, balB, dB, sB, K, ti, lane);
     }
 }
 
@@ -750,9 +787,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             const uint32_t exc = inc - flen;
             const uint32_t total = __shfl_sync(FULL, inc, 31);
             KNN_PT(1);
-            for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-                const uint32_t t = t0 + lane;
-                const bool valid = t < total;
+            // flattened position t -> (sorted position, cell's query mask)
+            auto locate = [&](uint32_t t, bool valid, uint32_t &sp, uint32_t &cmo) {
                 int src = 0;
 #pragma unroll
                 for (int step = 16; step >= 1; step >>= 1) {
@@ -761,19 +797,45 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 }
                 const uint32_t sb = __shfl_sync(FULL, rb, src);
                 const uint32_t se = __shfl_sync(FULL, exc, src);
-                const uint32_t s = valid ? sb + (t - se) : 0u;
+                sp = valid ? sb + (t - se) : 0u;
                 const uint32_t cm = __shfl_sync(FULL, cmask, src);  // every lane takes part
-                const uint32_t tmask = __reduce_or_sync(FULL, valid ? cm : 0u);
-                float c[DIM];
-                if (valid) {
-                    load_point<DIM>(a.xsort, s, c);
-                    st_cand += (unsigned long long)__popc(tmask);  // distances evaluated
-                    KNN_ITEM_TILE(__popc(tmask));
-                } else {
+                cmo = valid ? cm : 0u;
+            };
+            if (DIM >= S2_WIDE_DIM) {
+                for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+                    const bool vA = t0 + lane < total, vB = t0 + 32 + lane < total;
+                    uint32_t sA, sB, cmA, cmB;
+                    locate(t0 + lane, vA, sA, cmA);
+                    locate(t0 + 32 + lane, vB, sB, cmB);
+                    const uint32_t tmask = __reduce_or_sync(FULL, cmA | cmB);
+                    // lanes past the end get NaN coordinates: every distance
+                    // comparison with them is false
+                    float cA[DIM], cB[DIM];
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                    for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
+                    if (vA) load_point<DIM>(a.xsort, sA, cA);
+                    if (vB) load_point<DIM>(a.xsort, sB, cB);
+                    st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
+                    KNN_ITEM_TILE(__popc(tmask) * 2);
+                    scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane);
                 }
-                scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane);
+            } else {
+                for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                    const bool valid = t0 + lane < total;
+                    uint32_t s, cmo;
+                    locate(t0 + lane, valid, s, cmo);
+                    const uint32_t tmask = __reduce_or_sync(FULL, cmo);
+                    float c[DIM];
+                    if (valid) {
+                        load_point<DIM>(a.xsort, s, c);
+                        st_cand += (unsigned long long)__popc(tmask);  // distances evaluated
+                        KNN_ITEM_TILE(__popc(tmask));
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                    }
+                    scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane);
+                }
             }
             KNN_PT(2);
         }
