@@ -262,13 +262,17 @@ class Context:
                           out_dist.data_ptr())
         return out_ids, out_dist
 
-    def self_join_batch(self, point_list, Ks):
+    def self_join_batch(self, point_list, Ks, outs_in=None):
+        """Independent joins run concurrently by the context's worker pool.
+        outs_in: optional list of (ids, dist) output tensors (e.g. pinned host
+        buffers); returns the list of (ids, dist)."""
         torch = self._torch
         jobs, outs = [], []
-        for p, K in zip(point_list, Ks):
+        for q, (p, K) in enumerate(zip(point_list, Ks)):
             p = p.contiguous()
             n, d = p.shape
-            ids, dist = self._outputs(n, K, p, None, None)
+            given = outs_in[q] if outs_in is not None else (None, None)
+            ids, dist = self._outputs(n, K, p, given[0], given[1])
             outs.append((ids, dist))
             jobs.append(KnnjoinJob(p.data_ptr(), n, d, K, ids.data_ptr(), dist.data_ptr()))
         self._keep = point_list

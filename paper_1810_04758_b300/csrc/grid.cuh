@@ -610,6 +610,12 @@ __global__ void k_sqrt_rows(double *__restrict__ dist, int64_t count)
         u[i] = sqrt_bits(u[i]);
 }
 
+// Small readback: copy `words` 32-bit words (to mapped host memory).
+__global__ void k_fetch(uint32_t *dst, const uint32_t *__restrict__ src, int words)
+{
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
 __global__ void k_iota(uint32_t *out, int64_t m)
 {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;

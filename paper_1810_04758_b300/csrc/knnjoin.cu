@@ -66,7 +66,11 @@ struct Allocator {
     void *(*alloc)(size_t, void *) = nullptr;
     void (*free)(void *, void *) = nullptr;
     void *user = nullptr;
-    void *get(size_t bytes)
+    // without hooks: a stream-ordered pool owned by the context (allocation
+    // and release are ordered on the pipeline's stream and never synchronise
+    // the device, so pipelines of the worker pool do not stall each other)
+    cudaMemPool_t pool = nullptr;
+    void *get(size_t bytes, cudaStream_t s)
     {
         void *p = nullptr;
         if (alloc) {
@@ -74,24 +78,26 @@ struct Allocator {
             if (!p) fail(KNN_ERR_NOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
             return p;
         }
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
-            fail(KNN_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+            fail(KNN_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
         }
-        ck(e, "cudaMalloc");
+        ck(e, "device allocation");
         return p;
     }
-    void put(void *p)
+    void put(void *p, cudaStream_t s)
     {
         if (!p) return;
         if (free) free(p, user);
+        else if (pool) cudaFreeAsync(p, s);
         else cudaFree(p);
     }
 };
 
 struct Scratch {
     Allocator *al = nullptr;
+    cudaStream_t stream = nullptr;
     struct Buf {
         void *p = nullptr;
         size_t cap = 0;
@@ -103,18 +109,18 @@ struct Scratch {
         size_t bytes = std::max<size_t>(count * sizeof(T), 256);
         Buf &b = bufs[name];
         if (b.cap < bytes) {
-            al->put(b.p);
+            al->put(b.p, stream);
             b.p = nullptr;
             b.cap = 0;
             size_t nb = std::max(bytes, b.cap + b.cap / 4);
-            b.p = al->get(nb);
+            b.p = al->get(nb, stream);
             b.cap = nb;
         }
         return (T *)b.p;
     }
     void release()
     {
-        for (auto &kv : bufs) al->put(kv.second.p);
+        for (auto &kv : bufs) al->put(kv.second.p, stream);
         bufs.clear();
     }
 };
@@ -138,20 +144,32 @@ struct Pipeline {
     int nsm = 148;
     cudaStream_t s = nullptr;
     Scratch sc;
-    uint32_t *pinned = nullptr;  // small host readback area
+    uint32_t *pinned = nullptr;      // small host readback area
+    uint32_t *pinned_dev = nullptr;  // its device mapping (null: copy engine readbacks)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     knnjoin_stats stats{};
     float width_mult = 1.25f;
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
+    // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
+    // holds this token while its kernels run and releases it before copying
+    // its results to the host, so large joins take turns on the SMs and one
+    // join's copy overlaps the next one's kernels
+    std::mutex *big_token = nullptr;
+    static constexpr int64_t BIG_JOB_ENTRIES = (int64_t)1 << 25;
 
     void init(int dev, cudaStream_t stream, Allocator *al)
     {
         device = dev;
         s = stream;
         sc.al = al;
+        sc.stream = stream;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaMallocHost(&pinned, 4096));
+        // readbacks go through mapped host memory written by a one-warp
+        // kernel, so they never queue behind a large result copy of another
+        // join on the copy engines
+        CK(cudaHostAlloc(&pinned, 4096, cudaHostAllocMapped));
+        CK(cudaHostGetDevicePointer((void **)&pinned_dev, pinned, 0));
         for (auto &e : ev) CK(cudaEventCreate(&e));
         for (auto &e : evs) CK(cudaEventCreate(&e));
     }
@@ -166,10 +184,23 @@ struct Pipeline {
             if (e) cudaEventDestroy(e);
     }
 
+    // copy `bytes` (a multiple of 4) from device memory to host_dst, a
+    // position in `pinned`; complete once the stream is synchronised
+    void fetch(uint32_t *host_dst, const void *src, size_t bytes)
+    {
+        if (pinned_dev) {
+            k_fetch<<<1, 32, 0, s>>>(pinned_dev + (host_dst - pinned), (const uint32_t *)src, (int)(bytes / 4));
+            ++launches;
+        } else {
+            CK(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        }
+    }
+
     template <class T>
     T read1(const T *dev)
     {
-        CK(cudaMemcpyAsync(pinned, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+        static_assert(sizeof(T) % 4 == 0, "readback size");
+        fetch(pinned, dev, sizeof(T));
         CK(cudaStreamSynchronize(s));
         T v;
         memcpy(&v, pinned, sizeof(T));
@@ -352,6 +383,8 @@ void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
 
 void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in)
 {
+    std::unique_lock<std::mutex> turn;
+    if (big_token && n * (int64_t)K >= BIG_JOB_ENTRIES) turn = std::unique_lock<std::mutex>(*big_token);
     CK(cudaSetDevice(device));
     const bool pts_dev = is_device_ptr(pts_in);
     const bool ids_dev = is_device_ptr(ids_in);
@@ -503,7 +536,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         uint32_t *skey = sc.get<uint32_t>("skey", mm), *sval = sc.get<uint32_t>("sval", mm);
         uint32_t *skey2 = sc.get<uint32_t>("skey2", mm), *sval2 = sc.get<uint32_t>("sval2", mm);
         k_group_sizes<<<grid_for(mm, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
-        CK(cudaMemcpyAsync(pinned, small + 1, 8, cudaMemcpyDeviceToHost, s));
+        fetch(pinned, small + 1, 8);
         CK(cudaStreamSynchronize(s));
         uint32_t ng = pinned[0], maxsz = pinned[1];
         k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
@@ -511,8 +544,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
         k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
         scan(nit, ioff, ng);
-        CK(cudaMemcpyAsync(pinned, ioff + ng - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(pinned + 1, nit + ng - 1, 4, cudaMemcpyDeviceToHost, s));
+        fetch(pinned, ioff + ng - 1, 4);
+        fetch(pinned + 1, nit + ng - 1, 4);
         CK(cudaStreamSynchronize(s));
         nitems = pinned[0] + pinned[1];
         uint2 *items = sc.get<uint2>("items", nitems);
@@ -523,8 +556,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     auto select_list = [&](const uint32_t *list, int64_t mm, uint32_t value, uint32_t *out) -> int64_t {
         k_status_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, status, mm, value, flags); ++launches;
         scan(flags, rid, mm);
-        CK(cudaMemcpyAsync(pinned, rid + mm - 1, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(pinned + 1, flags + mm - 1, 4, cudaMemcpyDeviceToHost, s));
+        fetch(pinned, rid + mm - 1, 4);
+        fetch(pinned + 1, flags + mm - 1, 4);
         CK(cudaStreamSynchronize(s));
         int64_t cntv = (int64_t)pinned[0] + pinned[1];
         if (cntv > 0) {
@@ -543,7 +576,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
         k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
         k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
-        CK(cudaMemcpyAsync(pinned, small + 4, 8, cudaMemcpyDeviceToHost, s));
+        fetch(pinned, small + 4, 8);
         CK(cudaStreamSynchronize(s));
         const uint32_t lmin = pinned[0], lmax = pinned[1];
         if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
@@ -598,7 +631,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
             ms_scan += t;
             if (pass < 16) stats.ms_pass[pass] = t;
-            CK(cudaMemcpyAsync(pinned + 8, st, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            fetch(pinned + 8, st, sizeof(unsigned long long));
             CK(cudaStreamSynchronize(s));
             unsigned long long c;
             memcpy(&c, pinned + 8, sizeof(c));
@@ -628,9 +661,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.passes = pass;
     k_sqrt_rows<<<grid_for(n * K, 256, nsm, 16), 256, 0, s>>>(dist, n * K); ++launches;
     CK(cudaEventRecord(ev[2], s));
+    if (turn.owns_lock()) {
+        CK(cudaEventSynchronize(ev[2]));
+        turn.unlock();
+    }
     if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, s));
     if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * n * K, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(pinned, st, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    fetch(pinned, st, 4 * sizeof(unsigned long long));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     unsigned long long hs[4];
@@ -709,6 +746,7 @@ struct knnjoin_ctx {
     int nworkers = 8;
     int max_jobs = 1024;
     size_t budget = 0, in_use = 0;
+    std::mutex big_token;  // see Pipeline::big_token
 };
 
 // Device memory a join of n points holds while it runs (an estimate: the
@@ -791,6 +829,7 @@ static void start_workers(knnjoin_ctx *ctx)
         auto w = std::make_unique<Worker>();
         CK(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
         w->pipe.init(ctx->device, w->stream, &ctx->al);
+        w->pipe.big_token = &ctx->big_token;
         w->pipe.width_mult = ctx->main.width_mult;
         ctx->workers.push_back(std::move(w));
     }
@@ -862,6 +901,16 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
         ctx->al.user = ctx->cfg.user;
         if ((ctx->al.alloc == nullptr) != (ctx->al.free == nullptr))
             fail(KNN_ERR_INVALID, "alloc and free hooks must be given together");
+        if (!ctx->al.alloc) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = ctx->device;
+            CK(cudaMemPoolCreate(&ctx->al.pool, &props));
+            uint64_t keep = ~0ull;  // keep freed memory in the pool
+            CK(cudaMemPoolSetAttribute(ctx->al.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        }
         ctx->main.init(ctx->device, ctx->stream, &ctx->al);
         if (ctx->cfg.width_mult > 0.0f) ctx->main.width_mult = ctx->cfg.width_mult;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
@@ -893,10 +942,13 @@ void knnjoin_destroy(knnjoin_ctx *ctx)
     for (auto &w : ctx->workers) {
         cudaStreamSynchronize(w->stream);
         w->pipe.release();
+        cudaStreamSynchronize(w->stream);
         cudaStreamDestroy(w->stream);
     }
     ctx->main.release();
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->al.pool) cudaMemPoolDestroy(ctx->al.pool);
     delete ctx;
 }
 
@@ -1141,6 +1193,7 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
         P.nsm = D.nsm;
         P.s = (cudaStream_t)stream;
         P.sc.al = &al;
+        P.sc.stream = P.s;
         P.pinned = readback;
         for (int i = 0; i < 3; ++i) P.ev[i] = D.ev[i];
         P.evs[0] = D.ev[3];

@@ -566,8 +566,8 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
 // superset of what its threshold admits).
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const float (&cB)[DIM], uint32_t sA,
-                                                uint32_t sB, uint32_t tmask, uint64_t *buf,
-                                                float *qc, uint32_t *hist, int &my_cnt, int K, int lane)
+                                                uint32_t sB, uint32_t tmask, uint64_t *buf, float *qc,
+                                                uint32_t *hist, int &my_cnt, int K, int lane)
 {
     for (uint32_t m = tmask; m; m &= m - 1) {
         const int i = __ffs(m) - 1;
@@ -578,10 +578,13 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
         const float dB = dist2_f32<DIM>(qv, cB);
         const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
         const bool accB = dB <= ti && sB != qi_s;
-        const uint32_t balA = __ballot_sync(FULL, accA);
-        const uint32_t balB = __ballot_sync(FULL, accB);
-        if (balA) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
-        if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB, balB, dB, sB, K, ti, lane);
+        // one vote first for d >= 5, where a step usually accepts nothing
+        if (DIM < 5 || __any_sync(FULL, accA || accB)) {
+            const uint32_t balA = __ballot_sync(FULL, accA);
+            const uint32_t balB = __ballot_sync(FULL, accB);
+            if (balA) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
+            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB, balB, dB, sB, K, ti, lane);
+        }
     }
 }
 
