@@ -5,12 +5,12 @@
  * for every point p_i of a data set D of n points in d dimensions, find its K
  * nearest neighbours under the Euclidean distance, the point itself excluded.
  * This library computes it on one GPU with the paper's GPU method -- a grid
- * index built on the device (Sec. 3.1, 4.5), a search distance chosen from a
- * sampled distance histogram (Sec. 4.3), a density-ordered query work queue
- * (Sec. 4.4, Fig. 4) and a per-query scan of the 3^n adjacent cells (Alg. 1,
+ * index built on the device (Sec. 3.1, 4.6), a search distance chosen from a
+ * sampled distance histogram (Sec. 4.4), a density-ordered query work queue
+ * (Sec. 4.5, Fig. 4) and a per-query scan of the 3^n adjacent cells (Alg. 1,
  * GPUJoinKernel) -- made exact and self-contained: a query whose K-th
  * neighbour is not certified by the cells scanned is re-queued with a wider
- * ring of cells (the paper re-queues failed queries, Alg. 1, Sec. 4.4) until
+ * ring of cells (the paper re-queues failed queries, Alg. 1, Sec. 4.3) until
  * it is.
  *
  * Result convention (the paper fixes neither precision nor tie order; this
@@ -68,7 +68,7 @@ typedef struct {
     size_t hbm_budget_bytes;  /* admission limit of batched/served jobs; 0 = 90% of free memory */
     int max_jobs;             /* serving queue slots (jobs waiting to start); 0 = 1024 */
     const char *tune_cache_path; /* reserved */
-    float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.3); 0 = default */
+    float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.4); 0 = default */
     int workers;              /* concurrent join pipelines for batched/served jobs; 0 = 8 */
     int reserved[7];
 } knnjoin_config;
@@ -93,7 +93,7 @@ typedef struct {
     int64_t candidates;            /* candidate distance evaluations, all passes */
     int64_t band_entries;          /* exact re-scores (FP64-canonical) */
     int64_t overflow_queries;      /* queries redone with exact keys */
-    double eps_mean, eps_min;      /* Sec. 4.3 search distance */
+    double eps_mean, eps_min;      /* Sec. 4.4 search distance */
     double cell_width;             /* level-0 cell side */
     int key_bits;
     int fixed_point;               /* 1 = integer fast path for exact distances */

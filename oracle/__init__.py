@@ -164,7 +164,7 @@ def grid_rows(points: np.ndarray, K: int, rows, width_mult: float = 1.0, threads
 
 
 def select_epsilon(points: np.ndarray, K: int, threads: int = 0):
-    """(eps_min, eps_mean) of the paper's Sec. 4.3 procedure as the oracle reads it."""
+    """(eps_min, eps_mean) of the paper's Sec. 4.4 procedure as the oracle reads it."""
     p = _prep(points)
     n, d = p.shape
     em = ctypes.c_double(0.0)

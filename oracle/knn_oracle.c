@@ -23,7 +23,7 @@
  *   oracle_bf       brute force over all pairs (the definition written out).
  *   oracle_bf_rows  the same for a chosen subset of query rows.
  *   oracle_grid     an exact grid join in the paper's manner (Sec. 3.1 grid of
- *                   non-empty cells, Sec. 4.3 epsilon selection, ring of 3^n
+ *                   non-empty cells, Sec. 4.4 epsilon selection, ring of 3^n
  *                   adjacent cells, failed queries retried with a wider
  *                   search); it also counts the candidate distance
  *                   evaluations of that schedule.
@@ -149,7 +149,7 @@ int oracle_bf_rows(const float *pts, int64_t n, int d, int K,
 /* ------------------------------------------------------------------ */
 /* Grid join.                                                          */
 /*                                                                      */
-/* Search distance (Sec. 4.3): sample about 0.1% of D and take the mean */
+/* Search distance (Sec. 4.4): sample about 0.1% of D and take the mean */
 /* distance between the sampled points (eps_mean); histogram the        */
 /* distances from a fixed sample of points to every other point of D    */
 /* into n_bins bins of width eps_mean / n_bins (distances >= eps_mean   */

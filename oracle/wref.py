@@ -1,6 +1,6 @@
 """Reference-schedule work counts W_ref for the roofline -- TEST/BENCH INFRASTRUCTURE.
 
-Runs the oracle's grid join (width from the Sec. 4.3 selection with
+Runs the oracle's grid join (width from the Sec. 4.4 selection with
 multiplier 1, ring of 3^n cells, wider retry) on each named 2M-point
 workload and stores, per workload, the number of candidate distance
 evaluations and its pass profile in tests/golden/wref_2m.json.  Calls only

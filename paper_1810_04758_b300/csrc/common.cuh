@@ -21,7 +21,7 @@ struct GridParams {
     float lo[MAX_DIM], hi[MAX_DIM];  // bounding box (face origin = lo)
     int fixed_ok;                    // every coordinate is X * 2^-F, |X| < 2^30
     int F;
-    float eps_mean, eps_min;         // Sec. 4.3 search distance
+    float eps_mean, eps_min;         // Sec. 4.4 search distance
     float w0, inv_w0;                // level-0 cell side
     int cmax0[MAX_DIM];              // largest level-0 cell index per dimension
     int bits;                        // bits per dimension of the Morton key

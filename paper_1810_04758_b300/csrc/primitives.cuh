@@ -1,6 +1,6 @@
 // primitives.cuh -- prefix sums, stream compaction and LSD radix sort.
 //
-// Hand-written for the index build (Sec. 4.5: the grid is built on the GPU):
+// Hand-written for the index build (Sec. 4.6, GPU: Indexing: the grid is built on the GPU):
 // cell keys are sorted with an LSD radix sort on 8-bit digits (one pass per
 // digit of the bits actually used), and cell offsets come from exclusive
 // prefix sums over run flags.  Both use the reduce-then-scan pattern (no

@@ -1,5 +1,5 @@
 // scan.cuh -- the per-query neighbour-cell scan with top-K selection
-// (paper Alg. 1, GPUJoinKernel; Sec. 4.6 for several threads per query),
+// (paper Alg. 1, GPUJoinKernel; Sec. 4.7 for several threads per query),
 // made exact and self-certifying.
 //
 // One work item = up to WARPS queries that share a level-l grid cell (a slice

@@ -1,5 +1,5 @@
 // scan2.cuh -- register-reuse neighbour-cell scan with top-K selection
-// (paper Alg. 1 GPUJoinKernel, Sec. 4.6 task granularity), the fast path.
+// (paper Alg. 1 GPUJoinKernel, Sec. 4.7, GPU: Optimizing Task Granularity), the fast path.
 //
 // Each warp works alone (no block barriers) on work items of up to QM
 // queries that share a level-l grid cell:

@@ -72,6 +72,32 @@ def test_parity_small(ctx, kind, d, n, K):
     assert_same(run(ctx, p, K), oracle.bf(p, K))
 
 
+@pytest.mark.parametrize("d,K", [(2, 16), (3, 16), (4, 8)])
+def test_dense_core_in_sparse_background(ctx, d, K):
+    # 2/3 of the points in a cube of side 1e-3, the rest uniform: queries of
+    # the background sit at coarse levels whose ring covers the core, so the
+    # core's cells are long runs scanned in pruned super-tiles
+    n_core, n_bg = 20000, 10000
+    core = (0.5 + 1e-3 * gen.make_points("uniform", n_core, d, seed=31).astype(np.float64)).astype(np.float32)
+    bg = gen.make_points("uniform", n_bg, d, seed=32)
+    p = np.concatenate([core, bg])
+    assert_same(run(ctx, p, K), oracle.bf(p, K))
+
+
+def test_requeued_passes_match(ctx):
+    # queries that the first pass cannot certify are re-scanned one level up,
+    # starting from the band of the K-th value the first pass found
+    seen = 0
+    for kind, d, n, K in [("uniform", 6, 20000, 32), ("expo", 4, 20000, 64), ("expo", 2, 30000, 64)]:
+        p = gen.make_points(kind, n, d, seed=7)
+        got = run(ctx, p, K)
+        st = ctx.stats()
+        if st["passes"] >= 2 and st["pass_queries"][1] > 0:
+            seen += 1
+        assert_same(got, oracle.bf(p, K))
+    assert seen > 0
+
+
 @pytest.mark.parametrize("K", [1, 2, 255])
 def test_parity_k_extremes(ctx, K):
     p = gen.make_points("uniform", 3000, 3, seed=9)
