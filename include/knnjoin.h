@@ -126,6 +126,21 @@ void knnjoin_destroy(knnjoin_ctx *ctx);
 knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
                                  int32_t *out_ids, double *out_dist);
 
+/* R x S join (the same method with a query set apart from the data set;
+ * the paper notes, in Sec. 2.1, that its self-join applies directly to it):
+ * for each of the nq query points, the K nearest of the n data points under
+ * (D(r, j), j) ascending, j the data point's row.  Nothing is excluded: a
+ * query equal to a data point has it as a neighbour at distance 0.
+ *   queries  row-major float32 [nq][d], host or device;
+ *   points   row-major float32 [n][d], host or device;
+ *   out_ids  int32 [nq][K] (data rows), out_dist float64 [nq][K].
+ * The grid covers the bounding box of both sets; the search distance and the
+ * index are the data set's.  Returns KNN_ERR_INVALID for nq < 1, n < 2,
+ * n or nq > 2^31 - 1, d outside [1, 8], K outside [1, min(n, 256)], NULL
+ * pointers or a NaN/Inf coordinate in either set. */
+knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, const float *points, int64_t n,
+                            int d, int K, int32_t *out_ids, double *out_dist);
+
 /* Blocking: run njobs independent self-joins (same conventions as
  * knnjoin_self_join per job) concurrently on the context's worker pipelines
  * (each its own stream and scratch), admitted by device-memory footprint.

@@ -74,6 +74,9 @@ def _load(mutant: str | None = None) -> ctypes.CDLL:
             lib.oracle_bf_rows.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P,
                                            ctypes.c_int64, P, P, ctypes.c_int]
             lib.oracle_bf_rows.restype = ctypes.c_int
+            lib.oracle_bf_rs.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         P, P, ctypes.c_int]
+            lib.oracle_bf_rs.restype = ctypes.c_int
             lib.oracle_grid.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, P, P, P, ctypes.c_int]
             lib.oracle_grid.restype = ctypes.c_int
@@ -110,6 +113,22 @@ def bf(points: np.ndarray, K: int, threads: int = 0, mutant: str | None = None):
     rc = _load(mutant).oracle_bf(_ptr(p), n, d, K, _ptr(ids), _ptr(dist), threads)
     if rc:
         raise ValueError("oracle_bf: invalid arguments")
+    return ids, dist
+
+
+def bf_rs(queries: np.ndarray, points: np.ndarray, K: int, threads: int = 0, mutant: str | None = None):
+    """Brute-force R x S join: for each query row, the K nearest data rows
+    (ids into `points`, nothing excluded); arrays [len(queries), K]."""
+    q, p = _prep(queries), _prep(points)
+    if q.shape[1] != p.shape[1]:
+        raise ValueError("queries and points must have the same d")
+    nq, d = q.shape
+    n = p.shape[0]
+    ids = np.empty((nq, K), np.int32)
+    dist = np.empty((nq, K), np.float64)
+    rc = _load(mutant).oracle_bf_rs(_ptr(q), nq, _ptr(p), n, d, K, _ptr(ids), _ptr(dist), threads)
+    if rc:
+        raise ValueError("oracle_bf_rs: invalid arguments")
     return ids, dist
 
 

@@ -22,6 +22,10 @@
  * Functions:
  *   oracle_bf       brute force over all pairs (the definition written out).
  *   oracle_bf_rows  the same for a chosen subset of query rows.
+ *   oracle_bf_rs    brute force of the R x S join: for each query point of
+ *                   a set R, the K nearest points of a data set S under the
+ *                   same order, nothing excluded (the self-join applied to a
+ *                   query set apart from the data, as Sec. 2.1 notes).
  *   oracle_grid     an exact grid join in the paper's manner (Sec. 3.1 grid of
  *                   non-empty cells, Sec. 4.4 epsilon selection, ring of 3^n
  *                   adjacent cells, failed queries retried with a wider
@@ -141,6 +145,29 @@ int oracle_bf_rows(const float *pts, int64_t n, int d, int K,
         #pragma omp for schedule(dynamic, 1)
         for (int64_t r = 0; r < nrows; ++r)
             bf_one(pts, n, d, K, rows[r], top, ids + r * K, dist + r * K);
+        free(top);
+    }
+    return 0;
+}
+
+/* R x S: every pair (r, j), ranked by (D(r, j), j); no exclusion. */
+int oracle_bf_rs(const float *qry, int64_t nq, const float *pts, int64_t n, int d, int K,
+                 int32_t *ids, double *dist, int nthreads)
+{
+    if (!qry || !pts || !ids || !dist || nq < 1 || n < 1 || d < 1 || K < 1 || K > n)
+        return -1;
+    int nt = threads_or_default(nthreads);
+    #pragma omp parallel num_threads(nt)
+    {
+        nb_t *top = (nb_t *)malloc(sizeof(nb_t) * (size_t)K);
+        #pragma omp for schedule(dynamic, 64)
+        for (int64_t r = 0; r < nq; ++r) {
+            int cnt = 0;
+            const float *q = qry + r * d;
+            for (int64_t j = 0; j < n; ++j)
+                topk_insert(top, &cnt, K, canon_d2(q, pts + j * d, d), (int32_t)j);
+            write_row(top, K, ids + r * K, dist + r * K);
+        }
         free(top);
     }
     return 0;

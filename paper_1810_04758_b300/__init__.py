@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_NOMEM", 3: "KNN_E
                 7: "KNN_ERR_QUEUE_FULL"}
 
 # Every symbol include/knnjoin.h declares.
-EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_self_join_batch",
+EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_join", "knnjoin_self_join_batch",
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc")
 KNN_NOALLOC_MAX_POINTS = 65536
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_destroy.restype = None
     lib.knnjoin_self_join.argtypes = [P, P, I64, I, I, P, P]
     lib.knnjoin_self_join.restype = I
+    lib.knnjoin_join.argtypes = [P, P, I64, P, I64, I, I, P, P]
+    lib.knnjoin_join.restype = I
     lib.knnjoin_self_join_batch.argtypes = [P, ctypes.POINTER(KnnjoinJob), I]
     lib.knnjoin_self_join_batch.restype = I
     lib.knnjoin_submit.argtypes = [P, ctypes.POINTER(KnnjoinJob), ctypes.POINTER(ctypes.c_uint64)]
@@ -153,6 +155,11 @@ def _check(ctx: int, st: int) -> int:
 def knnjoin_self_join(ctx: int, points: int, n: int, d: int, K: int, out_ids: int,
                       out_dist: int) -> int:
     return _check(ctx, load_library().knnjoin_self_join(ctx, points, n, d, K, out_ids, out_dist))
+
+
+def knnjoin_join(ctx: int, queries: int, nq: int, points: int, n: int, d: int, K: int, out_ids: int,
+                 out_dist: int) -> int:
+    return _check(ctx, load_library().knnjoin_join(ctx, queries, nq, points, n, d, K, out_ids, out_dist))
 
 
 def knnjoin_self_join_batch(ctx: int, jobs: list[KnnjoinJob]) -> int:
@@ -260,6 +267,24 @@ class Context:
         out_ids, out_dist = self._outputs(n, K, points, out_ids, out_dist)
         knnjoin_self_join(self.ctx, points.data_ptr(), n, d, K, out_ids.data_ptr(),
                           out_dist.data_ptr())
+        return out_ids, out_dist
+
+    def join(self, queries, points, K: int, out_ids=None, out_dist=None):
+        """R x S join: for each row of the float32 [nq, d] `queries`, the K
+        nearest rows of the float32 [n, d] `points` (nothing excluded).
+        Returns (ids int32 [nq, K], dist float64 [nq, K]) on the queries' device."""
+        torch = self._torch
+        for t in (queries, points):
+            if t.dtype != torch.float32 or t.dim() != 2:
+                raise ValueError("queries and points must be float32 [rows, d] tensors")
+        if queries.shape[1] != points.shape[1]:
+            raise ValueError("queries and points must have the same d")
+        queries, points = queries.contiguous(), points.contiguous()
+        nq, d = queries.shape
+        n = points.shape[0]
+        out_ids, out_dist = self._outputs(nq, K, queries, out_ids, out_dist)
+        knnjoin_join(self.ctx, queries.data_ptr(), nq, points.data_ptr(), n, d, K, out_ids.data_ptr(),
+                     out_dist.data_ptr())
         return out_ids, out_dist
 
     def self_join_batch(self, point_list, Ks, outs_in=None):

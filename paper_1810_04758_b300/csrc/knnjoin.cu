@@ -235,7 +235,10 @@ struct Pipeline {
         }
     }
 
-    void run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in);
+    // self-join of the n points, or (qry_in != null) the K nearest of the n
+    // points for each of the nq query points
+    void run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
+             const float *qry_in = nullptr, int64_t nq_in = 0);
 };
 
 __global__ void k_init_reduce(PrepReduce *r)
@@ -381,10 +384,13 @@ void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
     }
 }
 
-void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in)
+void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
+                   const float *qry_in, int64_t nq_in)
 {
+    const bool self = qry_in == nullptr;
+    const int64_t nq = self ? n : nq_in;  // queries (output rows)
     std::unique_lock<std::mutex> turn;
-    if (big_token && n * (int64_t)K >= BIG_JOB_ENTRIES) turn = std::unique_lock<std::mutex>(*big_token);
+    if (big_token && nq * (int64_t)K >= BIG_JOB_ENTRIES) turn = std::unique_lock<std::mutex>(*big_token);
     CK(cudaSetDevice(device));
     const bool pts_dev = is_device_ptr(pts_in);
     const bool ids_dev = is_device_ptr(ids_in);
@@ -392,7 +398,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     memset(&stats, 0, sizeof(stats));
     launches = 0;
     double ms_scan = 0.0;
-    stats.n = n;
+    stats.n = nq;
     stats.d = d;
     stats.K = K;
 
@@ -402,8 +408,17 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         CK(cudaMemcpyAsync(p, pts_in, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
         pts = p;
     }
-    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)n * K);
-    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)n * K);
+    const float *qry = pts;
+    if (!self) {
+        qry = qry_in;
+        if (!is_device_ptr(qry_in)) {
+            float *p = sc.get<float>("qry_in", (size_t)nq * d);
+            CK(cudaMemcpyAsync(p, qry_in, sizeof(float) * nq * d, cudaMemcpyHostToDevice, s));
+            qry = p;
+        }
+    }
+    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)nq * K);
+    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)nq * K);
     CK(cudaEventRecord(ev[0], s));
 
     // a1
@@ -414,6 +429,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     k_init_reduce<<<1, 256, 0, s>>>(red); ++launches;
     float *xs = sc.get<float>("xs", (size_t)n * d);
     k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red); ++launches;
+    // R x S: the bounding box and fixed-point frame cover the queries too, so
+    // every query lies in the grid; the search distance and the index are
+    // the data set's
+    float *rxs = nullptr;
+    if (!self) {
+        rxs = sc.get<float>("rxs", (size_t)nq * d);
+        k_prep<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qry, nq, d, rxs, red); ++launches;
+    }
     // a2
     int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
     smp = std::min(smp, n);
@@ -455,12 +478,30 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
     float *xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
     k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
+    // queries: keys on the data grid, sorted, gathered (the data arrays for a self-join)
+    uint64_t *qkeys = keys;
+    uint32_t *qperm = perm;
+    float *qxsort = xsort;
+    if (!self) {
+        uint64_t *ralt = sc.get<uint64_t>("rkeys_alt", nq);
+        uint32_t *rpalt = sc.get<uint32_t>("rperm_alt", nq);
+        qkeys = sc.get<uint64_t>("rkeys", nq);
+        qperm = sc.get<uint32_t>("rperm", nq);
+        k_keys<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, gp, qkeys, qperm); ++launches;
+        radix_sort<uint64_t>(qkeys, qperm, ralt, rpalt, nq, hp.key_bits);
+        qxsort = sc.get<float>("rxsort", (size_t)nq * pad_dim(d));
+        k_gather<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, d, qperm, qxsort); ++launches;
+    }
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[1], s));
 
     // start level of every query (sliding-window cell counts)
-    uint32_t *lvl = sc.get<uint32_t>("lvl", n);
-    {
+    uint32_t *lvl = sc.get<uint32_t>("lvl", nq);
+    if (!self) {
+        // R x S: every query starts at the search-distance width (queries in
+        // sparse regions move up a level per pass until certified)
+        k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, hp.start_level); ++launches;
+    } else {
         // target count of a query's parent cell: between the expected counts
         // of the ideal level's parent and of the ideal level itself
         const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
@@ -481,17 +522,19 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     }
 
     // pass loop
-    uint32_t *active = sc.get<uint32_t>("active", n), *active2 = sc.get<uint32_t>("active2", n);
-    uint32_t *ovl = sc.get<uint32_t>("ovl", n);
-    uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
+    // query-side arrays are indexed by sorted query position
+    const int64_t nmax = std::max(n, nq);
+    uint32_t *active = sc.get<uint32_t>("active", nq), *active2 = sc.get<uint32_t>("active2", nq);
+    uint32_t *ovl = sc.get<uint32_t>("ovl", nq);
+    uint32_t *flags = sc.get<uint32_t>("flags", nmax), *rid = sc.get<uint32_t>("rid", nmax);
     uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
     uint32_t *small = sc.get<uint32_t>("small", 16);
-    uint32_t *status = sc.get<uint32_t>("fail", n);  // per sorted position
-    float *seed = sc.get<float>("seed", n);           // per sorted position, +inf to start
-    k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>((uint32_t *)seed, n, 0x7f800000u); ++launches;
-    uint32_t *lkey = sc.get<uint32_t>("lkey", n), *lkey2 = sc.get<uint32_t>("lkey2", n);
-    k_iota<<<grid_for(n, 256, nsm), 256, 0, s>>>(active, n); ++launches;
-    int64_t m = n;
+    uint32_t *status = sc.get<uint32_t>("fail", nq);  // per sorted query position
+    float *seed = sc.get<float>("seed", nq);           // per sorted query position, +inf to start
+    k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>((uint32_t *)seed, nq, 0x7f800000u); ++launches;
+    uint32_t *lkey = sc.get<uint32_t>("lkey", nq), *lkey2 = sc.get<uint32_t>("lkey2", nq);
+    k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
+    int64_t m = nq;
     // general kernel (scan.cuh)
     const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
     const int CH = d <= 6 ? 1024 : 512;
@@ -529,7 +572,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // work items of a (level, position)-ordered list of sorted positions
     auto make_items = [&](const uint32_t *list, int64_t mm, int qpi, uint32_t &nitems) -> uint2 * {
         uint32_t *gbegin = sc.get<uint32_t>("gbegin", mm + 1);
-        k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(keys, list, lvl, mm, d, flags); ++launches;
+        k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(qkeys, list, lvl, mm, d, flags); ++launches;
         scan(flags, rid, mm);
         k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
         CK(cudaMemsetAsync(small + 2, 0, 4, s));
@@ -592,6 +635,10 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         a.xsort = xsort;
         a.perm = perm;
         a.keys = keys;
+        a.qxsort = qxsort;
+        a.qkeys = qkeys;
+        a.qperm = qperm;
+        a.self = self ? 1 : 0;
         a.counter = small + 3;
         for (int L = 0; L < MAX_LEVELS; ++L) {
             a.hslotL[L] = tabs[L].slot;
@@ -659,14 +706,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     }
     stats.start_level = first_level;
     stats.passes = pass;
-    k_sqrt_rows<<<grid_for(n * K, 256, nsm, 16), 256, 0, s>>>(dist, n * K); ++launches;
+    k_sqrt_rows<<<grid_for(nq * K, 256, nsm, 16), 256, 0, s>>>(dist, nq * K); ++launches;
     CK(cudaEventRecord(ev[2], s));
     if (turn.owns_lock()) {
         CK(cudaEventSynchronize(ev[2]));
         turn.unlock();
     }
-    if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, s));
-    if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * n * K, cudaMemcpyDeviceToHost, s));
+    if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s));
+    if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * nq * K, cudaMemcpyDeviceToHost, s));
     fetch(pinned, st, 4 * sizeof(unsigned long long));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
@@ -692,6 +739,18 @@ void validate(const float *points, int64_t n, int d, int K, const int32_t *ids, 
     if (d < 1 || d > MAX_DIM) fail(KNN_ERR_INVALID, "d must be in [1, 8]");
     if (K < 1 || K > 256) fail(KNN_ERR_INVALID, "K must be in [1, 256]");
     if ((int64_t)K > n - 1) fail(KNN_ERR_INVALID, "K must be <= n - 1");
+}
+
+void validate_join(const float *queries, int64_t nq, const float *points, int64_t n, int d, int K,
+                   const int32_t *ids, const double *dist)
+{
+    if (!queries || !points || !ids || !dist) fail(KNN_ERR_INVALID, "NULL pointer argument");
+    if (nq < 1) fail(KNN_ERR_INVALID, "nq must be >= 1");
+    if (n < 2) fail(KNN_ERR_INVALID, "n must be >= 2");
+    if (n > 2147483647LL || nq > 2147483647LL) fail(KNN_ERR_INVALID, "n and nq must be <= 2^31 - 1");
+    if (d < 1 || d > MAX_DIM) fail(KNN_ERR_INVALID, "d must be in [1, 8]");
+    if (K < 1 || K > 256) fail(KNN_ERR_INVALID, "K must be in [1, 256]");
+    if ((int64_t)K > n) fail(KNN_ERR_INVALID, "K must be <= n");
 }
 
 }  // namespace
@@ -959,6 +1018,16 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
     return guard(ctx, [&] {
         validate(points, n, d, K, out_ids, out_dist);
         ctx->main.run(points, n, d, K, out_ids, out_dist);
+    });
+}
+
+knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, const float *points, int64_t n,
+                            int d, int K, int32_t *out_ids, double *out_dist)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        validate_join(queries, nq, points, n, d, K, out_ids, out_dist);
+        ctx->main.run(points, n, d, K, out_ids, out_dist, queries, nq);
     });
 }
 

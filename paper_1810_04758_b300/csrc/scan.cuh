@@ -58,6 +58,11 @@ struct ScanArgs {
     float w0;
     int fixed_ok, F;
     int B;                     // buffer entries per query (power of two, >= max(128, 2K))
+    // queries: their own sorted arrays (the data arrays above for a self-join)
+    const float *qxsort;       // query coordinates in query-key order, padded rows
+    const uint64_t *qkeys;     // sorted query keys on the data grid
+    const uint32_t *qperm;     // query key order -> original query row
+    int self;                  // 1: self-join (a query's own point is not its neighbour)
     int CH;                    // staged candidates per chunk
     int noff;                  // 3^d
 };
@@ -207,10 +212,11 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
         const bool has_q = (uint32_t)warp < (it.y & 0xffffu);
         const uint32_t qa = it.x + warp;
         const uint32_t qs = has_q ? a.active[qa] : 0u;
+        const uint32_t qself = a.self ? qs : 0xffffffffu;  // data position excluded
 
         if (tid == 0) {
             int c[MAX_DIM];
-            morton_decode(a.keys[a.active[it.x]] >> shift, DIM, nbits, c);
+            morton_decode(a.qkeys[a.active[it.x]] >> shift, DIM, nbits, c);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) s_cell[k] = c[k];
             s_exact = 0;
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
         int32_t qi[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            q[k] = a.xsort[(int64_t)qs * pad_dim(DIM) + k];
+            q[k] = a.qxsort[(int64_t)qs * pad_dim(DIM) + k];
             qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
         }
 
@@ -300,7 +306,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                         const int t = base + lane;
                         bool valid = t < clen;
                         uint32_t s = valid ? cs[t] : 0u;
-                        valid = valid && s != qs;
+                        valid = valid && s != qself;
                         if (!exact_round) {
                             float d2 = 0.0f;
                             if (valid) {
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 }
             }
             if (certified) {
-                const int64_t row = (int64_t)a.perm[qs] * K;
+                const int64_t row = (int64_t)a.qperm[qs] * K;
                 for (int u = 0; u < mine; ++u)
                     if (rr[u] < (uint32_t)K) {
                         a.out_ids[row + rr[u]] = (int32_t)rid[u];

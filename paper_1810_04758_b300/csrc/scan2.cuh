@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
         if (lane < Q) {
             uint32_t s = a.active[it.x + lane];
             float c[DIM];
-            load_point<DIM>(a.xsort, s, c);
+            load_point<DIM>(a.qxsort, s, c);
             qsv[lane] = s;
 #pragma unroll
             for (int k = 0; k < DIM; ++k) qc[lane * QP + k] = c[k];
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
         // in shared memory (cellv) rather than registers across the scan
         {
             int cell[DIM];
-            morton_decode(a.keys[qsv[0]] >> shift, DIM, nbits, cell);
+            morton_decode(a.qkeys[qsv[0]] >> shift, DIM, nbits, cell);
             if (lane < DIM) {
 #pragma unroll
                 for (int k = 0; k < DIM; ++k)
@@ -700,7 +700,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                                    ? __int_as_float(0x7f800000)
                                    : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
             qc[lane * QP + DIM] = fminf(thr0, a.seed[qsv[lane]]);
-            qc[lane * QP + DIM + 1] = __uint_as_float(qsv[lane]);
+            // the data position a candidate must not equal (none for R x S)
+            qc[lane * QP + DIM + 1] = __uint_as_float(a.self ? qsv[lane] : 0xffffffffu);
         }
         __syncwarp();
 
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 const uint32_t cmk = __shfl_sync(FULL, cmask, src);
                 const int nst = (int)((ce - cb + S2_SUPER - 1) / S2_SUPER);
                 const uint32_t sq = qsv[0];
-                const int u0 = (sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
+                const int u0 = (a.self && sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
                 for (int j = 0, left = nst; left > 0; ++j) {
                     const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
                     if (u < 0 || u >= nst) continue;
@@ -942,7 +943,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
                 if (certified) {
                     flag = 0;
-                    const int64_t row = (int64_t)a.perm[qsv[i]] * K;
+                    const int64_t row = (int64_t)a.qperm[qsv[i]] * K;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int g = lane * E + e;

@@ -77,6 +77,50 @@ def test_bf_full_sort_is_k_equals_n_minus_1():
     np.testing.assert_array_equal(ids, eids)
 
 
+def exact_knn_rs(queries, points, K):
+    """Exact rational (distance^2, id) ranking of every (query, data point)
+    pair, nothing excluded."""
+    qs = [[Fraction(float(v)) for v in row] for row in queries]
+    ps = [[Fraction(float(v)) for v in row] for row in points]
+    ids = np.empty((len(qs), K), np.int32)
+    d2 = [[None] * K for _ in range(len(qs))]
+    for r, q in enumerate(qs):
+        cand = sorted((sum((a - b) ** 2 for a, b in zip(q, p)), j) for j, p in enumerate(ps))
+        for k in range(K):
+            ids[r, k] = cand[k][1]
+            d2[r][k] = cand[k][0]
+    return ids, d2
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 6])
+@pytest.mark.parametrize("nq,n,K", [(7, 20, 1), (25, 40, 9), (30, 12, 12)])
+def test_bf_rs_matches_exact_rational(d, nq, n, K):
+    # R x S on the coarse dyadic grid: ties everywhere, K up to n (no exclusion)
+    q = quantized(nq, d, seed=100 + d)
+    p = quantized(n, d, seed=200 + d)
+    ids, dist = oracle.bf_rs(q, p, K)
+    eids, ed2 = exact_knn_rs(q, p, K)
+    np.testing.assert_array_equal(ids, eids)
+    for r in range(nq):
+        for k in range(K):
+            assert dist[r, k] == math.sqrt(float(ed2[r][k]))
+
+
+@pytest.mark.parametrize("kind,d", [("uniform", 3), ("expo", 2), ("clustered2d", 2)])
+def test_bf_rs_of_a_set_with_itself_is_the_self_join(kind, d):
+    # R = S with K + 1 neighbours: each row holds the query's own index; with
+    # it removed the row is the self-join's row (pinned above)
+    p = gen.make_points(kind, 600, d, seed=5)
+    K = 12
+    ids_rs, dist_rs = oracle.bf_rs(p, p, K + 1)
+    ids, dist = oracle.bf(p, K)
+    for i in range(len(p)):
+        keep = ids_rs[i] != i
+        assert (~keep).sum() == 1
+        np.testing.assert_array_equal(ids_rs[i][keep], ids[i])
+        np.testing.assert_array_equal(dist_rs[i][keep], dist[i])
+
+
 def test_exact_vs_canonical_on_generic_floats():
     """On generic (non-dyadic-grid) floats canonical FP64 may in principle
     reorder near-equal distances; count how often -- expected 0 here."""
