@@ -67,8 +67,12 @@ typedef struct {
     void *user;
     size_t hbm_budget_bytes;  /* admission limit of batched/served jobs; 0 = 90% of free memory */
     int max_jobs;             /* serving queue slots (jobs waiting to start); 0 = 1024 */
-    const char *tune_cache_path; /* reserved */
-    float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.4); 0 = default */
+    const char *tune_cache_path; /* JSON file of autotuned cell-width multipliers:
+                                    read at create, rewritten by knnjoin_autotune;
+                                    NULL = tuning kept in memory only */
+    float width_mult;         /* cell side = width_mult * eps_min (Sec. 4.4); 0 = the
+                                 autotuned value for (d, K, floor(log2 n)) if any,
+                                 else 1.25.  Speed only: results never depend on it */
     int workers;              /* concurrent join pipelines for batched/served jobs; 0 = 8 */
     int reserved[7];
 } knnjoin_config;
@@ -105,6 +109,7 @@ typedef struct {
     double ms_wall;                /* served/batched: submit -> done (host clock) */
     double ms_pass[16];            /* device time of each pass's scan launches */
     int64_t pass_candidates[16];   /* candidate distance evaluations of each pass */
+    double width_mult;             /* cell-width multiplier the join used */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).
@@ -140,6 +145,16 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
  * pointers or a NaN/Inf coordinate in either set. */
 knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, const float *points, int64_t n,
                             int d, int K, int32_t *out_ids, double *out_dist);
+
+/* Autotuning (not in the paper; its analogue is the search-distance factor
+ * study of Sec. 5.4): time the self-join of these points at a fixed list of
+ * cell-width multipliers (1.0 .. 1.625, best of two runs each, outputs in
+ * library scratch), keep the fastest for the key (d, K, floor(log2 n)) -- used
+ * by later joins of the context (and its worker pool) unless the config fixed
+ * width_mult -- and rewrite tune_cache_path if set.  Same validation as
+ * knnjoin_self_join; *best_width_mult receives the chosen multiplier. */
+knnjoin_status knnjoin_autotune(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                float *best_width_mult);
 
 /* Blocking: run njobs independent self-joins (same conventions as
  * knnjoin_self_join per job) concurrently on the context's worker pipelines

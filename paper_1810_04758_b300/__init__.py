@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_NOMEM", 3: "KNN_E
                 7: "KNN_ERR_QUEUE_FULL"}
 
 # Every symbol include/knnjoin.h declares.
-EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_join", "knnjoin_self_join_batch",
+EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_join", "knnjoin_autotune",
+           "knnjoin_self_join_batch",
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc")
 KNN_NOALLOC_MAX_POINTS = 65536
@@ -60,7 +61,8 @@ class KnnjoinStats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("ms_queue", ctypes.c_double),
                 ("ms_wall", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16),
-                ("pass_candidates", ctypes.c_int64 * 16)]
+                ("pass_candidates", ctypes.c_int64 * 16),
+                ("width_mult", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -102,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_self_join.restype = I
     lib.knnjoin_join.argtypes = [P, P, I64, P, I64, I, I, P, P]
     lib.knnjoin_join.restype = I
+    lib.knnjoin_autotune.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_float)]
+    lib.knnjoin_autotune.restype = I
     lib.knnjoin_self_join_batch.argtypes = [P, ctypes.POINTER(KnnjoinJob), I]
     lib.knnjoin_self_join_batch.restype = I
     lib.knnjoin_submit.argtypes = [P, ctypes.POINTER(KnnjoinJob), ctypes.POINTER(ctypes.c_uint64)]
@@ -162,6 +166,12 @@ def knnjoin_join(ctx: int, queries: int, nq: int, points: int, n: int, d: int, K
     return _check(ctx, load_library().knnjoin_join(ctx, queries, nq, points, n, d, K, out_ids, out_dist))
 
 
+def knnjoin_autotune(ctx: int, points: int, n: int, d: int, K: int) -> float:
+    best = ctypes.c_float(0.0)
+    _check(ctx, load_library().knnjoin_autotune(ctx, points, n, d, K, ctypes.byref(best)))
+    return float(best.value)
+
+
 def knnjoin_self_join_batch(ctx: int, jobs: list[KnnjoinJob]) -> int:
     arr = (KnnjoinJob * len(jobs))(*jobs)
     return _check(ctx, load_library().knnjoin_self_join_batch(ctx, arr, len(jobs)))
@@ -208,7 +218,8 @@ class Context:
     current stream on it."""
 
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
-                 max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0):
+                 max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0,
+                 tune_cache_path: Optional[str] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -224,6 +235,8 @@ class Context:
         cfg.max_jobs = max_jobs
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.workers = workers
+        self._tune_path = tune_cache_path.encode() if tune_cache_path else None
+        cfg.tune_cache_path = self._tune_path
         self._cfg = cfg
         self.ctx = knnjoin_create(cfg)
 
@@ -268,6 +281,14 @@ class Context:
         knnjoin_self_join(self.ctx, points.data_ptr(), n, d, K, out_ids.data_ptr(),
                           out_dist.data_ptr())
         return out_ids, out_dist
+
+    def autotune(self, points, K: int) -> float:
+        """Time the self-join of `points` at several cell-width multipliers and
+        keep the fastest for later joins of the same (d, K, log2 n) class;
+        returns it.  Results never depend on the multiplier."""
+        points = points.contiguous()
+        n, d = points.shape
+        return knnjoin_autotune(self.ctx, points.data_ptr(), n, d, K)
 
     def join(self, queries, points, K: int, out_ids=None, out_dist=None):
         """R x S join: for each row of the float32 [nq, d] `queries`, the K

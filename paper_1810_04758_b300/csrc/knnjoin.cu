@@ -19,6 +19,7 @@
 #include <deque>
 #include <functional>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <stdexcept>
@@ -137,6 +138,74 @@ bool is_device_ptr(const void *p)
 }
 
 // ---------------------------------------------------------------------------
+// Autotuned cell-width multipliers, keyed by (d, K, floor(log2 n)), shared by
+// a context's pipelines and kept in an optional JSON file.  The multiplier
+// only changes speed: results are identical for every value.
+// ---------------------------------------------------------------------------
+struct TuneTable {
+    std::mutex mu;
+    std::map<std::tuple<int, int, int>, float> wm;
+    std::string path;
+    float fixed = 0.0f;     // the caller's width_mult (> 0 overrides tuning)
+    float dflt = 1.25f;
+
+    static int nlog2(int64_t n)
+    {
+        int b = 0;
+        while (b < 62 && ((int64_t)1 << (b + 1)) <= n) ++b;
+        return b;
+    }
+    float lookup(int d, int K, int64_t n)
+    {
+        if (fixed > 0.0f) return fixed;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = wm.find(std::make_tuple(d, K, nlog2(n)));
+        return it == wm.end() ? dflt : it->second;
+    }
+    void set(int d, int K, int64_t n, float v)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        wm[std::make_tuple(d, K, nlog2(n))] = v;
+        save_locked();
+    }
+    // {"knnjoin_tune": 1, "entries": [{"d": 2, "K": 32, "nlog2": 20, "width_mult": 1.125}, ...]}
+    void load()
+    {
+        if (path.empty()) return;
+        FILE *f = fopen(path.c_str(), "r");
+        if (!f) return;
+        std::string text;
+        char buf[4096];
+        size_t got;
+        while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+        fclose(f);
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t at = text.find("{\"d\":"); at != std::string::npos; at = text.find("{\"d\":", at + 1)) {
+            int d = 0, K = 0, nl = 0;
+            float v = 0.0f;
+            if (sscanf(text.c_str() + at, "{\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %f", &d, &K,
+                       &nl, &v) == 4 && v > 0.0f && v < 16.0f)
+                wm[std::make_tuple(d, K, nl)] = v;
+        }
+    }
+    void save_locked()
+    {
+        if (path.empty()) return;
+        FILE *f = fopen(path.c_str(), "w");
+        if (!f) return;
+        fprintf(f, "{\"knnjoin_tune\": 1, \"entries\": [");
+        bool first = true;
+        for (auto &e : wm) {
+            fprintf(f, "%s\n {\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %.6g}", first ? "" : ",",
+                    std::get<0>(e.first), std::get<1>(e.first), std::get<2>(e.first), e.second);
+            first = false;
+        }
+        fprintf(f, "\n]}\n");
+        fclose(f);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // One join pipeline (stream + scratch + pinned readback).
 // ---------------------------------------------------------------------------
 struct Pipeline {
@@ -148,7 +217,9 @@ struct Pipeline {
     uint32_t *pinned_dev = nullptr;  // its device mapping (null: copy engine readbacks)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     knnjoin_stats stats{};
-    float width_mult = 1.25f;
+    float width_mult = 1.25f;      // used when no tune table is attached
+    TuneTable *tune = nullptr;
+    float force_wm = 0.0f;         // > 0: this multiplier (autotuning runs)
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
@@ -441,13 +512,15 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
     smp = std::min(smp, n);
     k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red); ++launches;
+    const float wmul = force_wm > 0.0f ? force_wm : (tune ? tune->lookup(d, K, n) : width_mult);
+    stats.width_mult = wmul;
     ParamsIn pin;
     pin.n = n;
     pin.d = d;
     pin.K = K;
     pin.S = std::min<int64_t>(n, 256);
     pin.m = std::min<int64_t>(n, 65536);
-    pin.width_mult = width_mult;
+    pin.width_mult = wmul;
     pin.start_level = 0;
     pin.max_finer = 3;
     float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
@@ -505,7 +578,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         // target count of a query's parent cell: between the expected counts
         // of the ideal level's parent and of the ideal level itself
         const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
-        const double ideal = std::pow(2.0 * (double)width_mult, d) * (double)K / Vd;
+        const double ideal = std::pow(2.0 * (double)wmul, d) * (double)K / Vd;
         int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
         if (hp.finer == 0) {
             // no density skew: every query starts at the search-distance width
@@ -731,9 +804,16 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.launches = launches;
 }
 
+void validate_sizes(int64_t n, int d, int K);
+
 void validate(const float *points, int64_t n, int d, int K, const int32_t *ids, const double *dist)
 {
     if (!points || !ids || !dist) fail(KNN_ERR_INVALID, "NULL pointer argument");
+    validate_sizes(n, d, K);
+}
+
+void validate_sizes(int64_t n, int d, int K)
+{
     if (n < 2) fail(KNN_ERR_INVALID, "n must be >= 2");
     if (n > 2147483647LL) fail(KNN_ERR_INVALID, "n must be <= 2^31 - 1");
     if (d < 1 || d > MAX_DIM) fail(KNN_ERR_INVALID, "d must be in [1, 8]");
@@ -806,6 +886,7 @@ struct knnjoin_ctx {
     int max_jobs = 1024;
     size_t budget = 0, in_use = 0;
     std::mutex big_token;  // see Pipeline::big_token
+    TuneTable tune;
 };
 
 // Device memory a join of n points holds while it runs (an estimate: the
@@ -890,6 +971,7 @@ static void start_workers(knnjoin_ctx *ctx)
         w->pipe.init(ctx->device, w->stream, &ctx->al);
         w->pipe.big_token = &ctx->big_token;
         w->pipe.width_mult = ctx->main.width_mult;
+        w->pipe.tune = &ctx->tune;
         ctx->workers.push_back(std::move(w));
     }
     for (auto &w : ctx->workers) {
@@ -972,6 +1054,10 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
         }
         ctx->main.init(ctx->device, ctx->stream, &ctx->al);
         if (ctx->cfg.width_mult > 0.0f) ctx->main.width_mult = ctx->cfg.width_mult;
+        ctx->tune.fixed = ctx->cfg.width_mult > 0.0f ? ctx->cfg.width_mult : 0.0f;
+        if (ctx->cfg.tune_cache_path) ctx->tune.path = ctx->cfg.tune_cache_path;
+        ctx->tune.load();
+        ctx->main.tune = &ctx->tune;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
         if (ctx->cfg.workers > 0) ctx->nworkers = std::min(ctx->cfg.workers, 64);
         size_t freeb = 0, totalb = 0;
@@ -1028,6 +1114,37 @@ knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, 
     return guard(ctx, [&] {
         validate_join(queries, nq, points, n, d, K, out_ids, out_dist);
         ctx->main.run(points, n, d, K, out_ids, out_dist, queries, nq);
+    });
+}
+
+knnjoin_status knnjoin_autotune(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                float *best_width_mult)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!best_width_mult || !points) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        Pipeline &P = ctx->main;
+        int32_t *ids = P.sc.get<int32_t>("tune_ids", (size_t)n * K);
+        double *dist = P.sc.get<double>("tune_dist", (size_t)n * K);
+        static const float cand[] = {1.0f, 1.0625f, 1.125f, 1.1875f, 1.25f, 1.3125f, 1.4f, 1.5f, 1.625f};
+        float best = ctx->tune.dflt;
+        double best_ms = 1e300;
+        for (float c : cand) {
+            P.force_wm = c;
+            double ms = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                P.run(points, n, d, K, ids, dist);
+                ms = std::min(ms, (double)P.stats.ms_total);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        P.force_wm = 0.0f;
+        if (ctx->tune.fixed <= 0.0f) ctx->tune.set(d, K, n, best);
+        *best_width_mult = best;
     });
 }
 
