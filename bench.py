@@ -304,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     def one_step(collect):
+        # the step's joins one blocking call after another (per-join stats)
         per = {}
         for nm in names:
             K = hosts[nm][1]
@@ -312,36 +313,49 @@ def run_ours(args, rank, world, local_rank):
                 per[nm] = ctx.stats()
         return per
 
+    plist, klist, olist = [dpts[nm] for nm in names], [hosts[nm][1] for nm in names], [outs[nm] for nm in names]
+
+    def batch_step():
+        # the step's joins through knnjoin_self_join_batch: the worker pool
+        # runs them on their own streams, so one join's index build and
+        # small passes overlap another's scan
+        ctx.self_join_batch(plist, klist, olist)
+
     for _ in range(max(args.warmup, 0)):
         one_step(False)
+        batch_step()
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    per_cfg = {nm: [] for nm in names}
-    launches = 0
-    scan_ms = 0.0
+    def timed_steps(fn, collect):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        pers = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            r = fn(collect) if collect else fn()
+            evs[i][1].record(stream)
+            pers.append(r)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], pers
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            per = one_step(True)
-            ev[i][1].record(stream)
-            for nm in names:
-                per_cfg[nm].append(per[nm])
-                launches += per[nm]["launches"]
-                scan_ms += per[nm]["ms_scan"]
+        step_ms, _ = timed_steps(batch_step, False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        seq_ms, pers = timed_steps(one_step, True)
+    per_cfg = {nm: [p[nm] for p in pers] for nm in names}
+    launches = sum(p[nm]["launches"] for p in pers for nm in names)
+    scan_ms = sum(p[nm]["ms_scan"] for p in pers for nm in names)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dev, world)
+    seq_ms_per_step = max_over_ranks(sum(seq_ms), dev, world) / args.steps
     nq_step = sum(len(hosts[nm][0]) for nm in names)
     ms_per_step = total_ms / args.steps
     value = world * nq_step / (ms_per_step / 1000.0)
@@ -473,6 +487,9 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "sequential_ms_per_step": seq_ms_per_step,
+        "step_api": "knnjoin_self_join_batch (the three joins on the worker pool); per-join stats, "
+                    "roofline and sequential_ms_per_step from the same joins as blocking calls",
         "clocks": clk.summary(),
         "per_config": per_summary,
         "wall_s_timed": round(wall, 3),

@@ -223,9 +223,9 @@ struct Pipeline {
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
-    // holds this token while its kernels run and releases it before copying
-    // its results to the host, so large joins take turns on the SMs and one
-    // join's copy overlaps the next one's kernels
+    // and host outputs holds this token while its kernels run and releases it
+    // before copying its results to the host, so such joins take turns on the
+    // SMs and one join's copy overlaps the next one's kernels
     std::mutex *big_token = nullptr;
     static constexpr int64_t BIG_JOB_ENTRIES = (int64_t)1 << 25;
 
@@ -460,12 +460,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
 {
     const bool self = qry_in == nullptr;
     const int64_t nq = self ? n : nq_in;  // queries (output rows)
-    std::unique_lock<std::mutex> turn;
-    if (big_token && nq * (int64_t)K >= BIG_JOB_ENTRIES) turn = std::unique_lock<std::mutex>(*big_token);
     CK(cudaSetDevice(device));
     const bool pts_dev = is_device_ptr(pts_in);
     const bool ids_dev = is_device_ptr(ids_in);
     const bool dist_dev = is_device_ptr(dist_in);
+    // large joins whose results go to host memory take turns (see big_token)
+    std::unique_lock<std::mutex> turn;
+    if (big_token && !(ids_dev && dist_dev) && nq * (int64_t)K >= BIG_JOB_ENTRIES)
+        turn = std::unique_lock<std::mutex>(*big_token);
     memset(&stats, 0, sizeof(stats));
     launches = 0;
     double ms_scan = 0.0;
