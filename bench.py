@@ -285,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    ctx = kj.Context(device=local_rank, stream=stream)
+    ctx = kj.Context(device=local_rank, stream=stream, policy=args.policy)
     names = WORKLOADS[args.workload]
     if args.configs:
         names = [nm for nm in names if nm in args.configs.split(",")]
@@ -298,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
     # cell-width autotuning (untimed, before the warm-up): the library times
     # the join at several multipliers and keeps the fastest per (d, K, log2 n)
     tuned = {}
-    if not args.no_autotune:
+    if not args.no_autotune and args.policy == 0:
         for nm in names:
             tuned[nm] = ctx.autotune(dpts[nm], hosts[nm][1])
         torch.cuda.synchronize()
@@ -487,6 +487,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "policy": "paper GPU-Only (global eps, re-index)" if args.policy == 1 else "certified rings",
         "sequential_ms_per_step": seq_ms_per_step,
         "step_api": "knnjoin_self_join_batch (the three joins on the worker pool); per-join stats, "
                     "roofline and sequential_ms_per_step from the same joins as blocking calls",
@@ -742,6 +743,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--policy", type=int, choices=[0, 1], default=0,
+                    help="1: the paper's GPU-Only policy (global eps, re-index eps += eps_min/2)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default cell-width multiplier instead of autotuning it first")
     ap.add_argument("--configs", default="",

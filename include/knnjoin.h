@@ -74,7 +74,14 @@ typedef struct {
                                  autotuned value for (d, K, floor(log2 n)) if any,
                                  else 1.25.  Speed only: results never depend on it */
     int workers;              /* concurrent join pipelines for batched/served jobs; 0 = 8 */
-    int reserved[7];
+    int policy;               /* 0: certified rings (default): a query is re-queued one level
+                                 up until its K-th neighbour is closer than the faces of its
+                                 scanned box.  1: the paper's GPU-Only policy (Alg. 1, Sec. 4.4):
+                                 one global eps (cell side eps, eps_0 = eps_min), a query fails
+                                 when fewer than K neighbours lie within eps, and failed queries
+                                 are redone on a grid re-indexed with eps += eps_min / 2.
+                                 Results are identical; speed differs */
+    int reserved[6];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */

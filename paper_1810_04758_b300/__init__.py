@@ -41,7 +41,8 @@ class KnnjoinConfig(ctypes.Structure):
                 ("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("user", ctypes.c_void_p),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
                 ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
-                ("workers", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("workers", ctypes.c_int), ("policy", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class KnnjoinJob(ctypes.Structure):
@@ -219,7 +220,7 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
                  max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0,
-                 tune_cache_path: Optional[str] = None):
+                 tune_cache_path: Optional[str] = None, policy: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -235,6 +236,7 @@ class Context:
         cfg.max_jobs = max_jobs
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.workers = workers
+        cfg.policy = policy
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None
         cfg.tune_cache_path = self._tune_path
         self._cfg = cfg

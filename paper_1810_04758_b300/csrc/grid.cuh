@@ -610,6 +610,24 @@ __global__ void k_sqrt_rows(double *__restrict__ dist, int64_t count)
         u[i] = sqrt_bits(u[i]);
 }
 
+// The paper's policy (epochs): flag the sorted positions whose query is not
+// done yet, and mark the queries certified by a pass as done.
+__global__ void k_undone_flags(const uint32_t *__restrict__ qperm, const uint32_t *__restrict__ done, int64_t nq,
+                               uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nq; a += (int64_t)gridDim.x * blockDim.x)
+        flags[a] = done[qperm[a]] == 0u;
+}
+
+__global__ void k_mark_done(const uint32_t *__restrict__ list, const uint32_t *__restrict__ status, int64_t m,
+                            const uint32_t *__restrict__ qperm, uint32_t *__restrict__ done)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = list[a];
+        if (status[s] == 0u) done[qperm[s]] = 1u;
+    }
+}
+
 // Small readback: copy `words` 32-bit words (to mapped host memory).
 __global__ void k_fetch(uint32_t *dst, const uint32_t *__restrict__ src, int words)
 {

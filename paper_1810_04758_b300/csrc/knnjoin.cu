@@ -220,6 +220,7 @@ struct Pipeline {
     float width_mult = 1.25f;      // used when no tune table is attached
     TuneTable *tune = nullptr;
     float force_wm = 0.0f;         // > 0: this multiplier (autotuning runs)
+    int policy = 0;                // knnjoin_config.policy
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
@@ -525,6 +526,11 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     pin.width_mult = wmul;
     pin.start_level = 0;
     pin.max_finer = 3;
+    if (policy == 1) {  // the paper's policy: cell side = eps = eps_min, one level
+        pin.width_mult = 1.0f;
+        pin.max_finer = 0;
+        stats.width_mult = 1.0;
+    }
     float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
     float *mrow = sc.get<float>("eps_mrow", (size_t)pin.m * 8);
     k_eps_rows<<<grid_for(pin.S + pin.m, 256, nsm), 256, 0, s>>>(xs, n, d, pin.S, pin.m, srow, mrow); ++launches;
@@ -546,238 +552,279 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.fixed_point = hp.fixed_ok;
     stats.start_level = hp.start_level;
 
-    // a3-a5
-    uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
-    uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
-    k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
-    radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
-    float *xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
-    k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
-    // queries: keys on the data grid, sorted, gathered (the data arrays for a self-join)
-    uint64_t *qkeys = keys;
-    uint32_t *qperm = perm;
-    float *qxsort = xsort;
-    if (!self) {
-        uint64_t *ralt = sc.get<uint64_t>("rkeys_alt", nq);
-        uint32_t *rpalt = sc.get<uint32_t>("rperm_alt", nq);
-        qkeys = sc.get<uint64_t>("rkeys", nq);
-        qperm = sc.get<uint32_t>("rperm", nq);
-        k_keys<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, gp, qkeys, qperm); ++launches;
-        radix_sort<uint64_t>(qkeys, qperm, ralt, rpalt, nq, hp.key_bits);
-        qxsort = sc.get<float>("rxsort", (size_t)nq * pad_dim(d));
-        k_gather<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, d, qperm, qxsort); ++launches;
-    }
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(ev[1], s));
-
-    // start level of every query (sliding-window cell counts)
-    uint32_t *lvl = sc.get<uint32_t>("lvl", nq);
-    if (!self) {
-        // R x S: every query starts at the search-distance width (queries in
-        // sparse regions move up a level per pass until certified)
-        k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, hp.start_level); ++launches;
-    } else {
-        // target count of a query's parent cell: between the expected counts
-        // of the ideal level's parent and of the ideal level itself
-        const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
-        const double ideal = std::pow(2.0 * (double)wmul, d) * (double)K / Vd;
-        int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
-        if (hp.finer == 0) {
-            // no density skew: every query starts at the search-distance width
-            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.start_level); ++launches;
-        } else if (n >= H && hp.top_level > 0) {
-            const int64_t nw = n - H + 1;
-            uint8_t *pm = sc.get<uint8_t>("win_pm", nw), *smn = sc.get<uint8_t>("win_sm", nw);
-            const int64_t nblk = (nw + H - 1) / H;
-            k_window_blocks<<<grid_for(nblk, 128, nsm, 16), 128, 0, s>>>(keys, nw, H, d, pm, smn); ++launches;
-            k_start_levels<<<grid_for(n, 256, nsm), 256, 0, s>>>(pm, smn, n, H, hp.top_level, hp.start_level, lvl); ++launches;
-        } else {
-            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.top_level); ++launches;
-        }
-    }
-
-    // pass loop
-    // query-side arrays are indexed by sorted query position
-    const int64_t nmax = std::max(n, nq);
-    uint32_t *active = sc.get<uint32_t>("active", nq), *active2 = sc.get<uint32_t>("active2", nq);
-    uint32_t *ovl = sc.get<uint32_t>("ovl", nq);
-    uint32_t *flags = sc.get<uint32_t>("flags", nmax), *rid = sc.get<uint32_t>("rid", nmax);
-    uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
-    uint32_t *small = sc.get<uint32_t>("small", 16);
-    uint32_t *status = sc.get<uint32_t>("fail", nq);  // per sorted query position
-    float *seed = sc.get<float>("seed", nq);           // per sorted query position, +inf to start
-    k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>((uint32_t *)seed, nq, 0x7f800000u); ++launches;
-    uint32_t *lkey = sc.get<uint32_t>("lkey", nq), *lkey2 = sc.get<uint32_t>("lkey2", nq);
-    k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
-    int64_t m = nq;
-    // general kernel (scan.cuh)
-    const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
-    const int CH = d <= 6 ? 1024 : 512;
-    int noff = 1;
-    for (int k = 0; k < d; ++k) noff *= 3;
-    const size_t smem1 = scan_smem_bytes(d, noff, CH, B1);
-    // fast kernel (scan2.cuh)
-    const bool fast = K + 32 <= 256;
-    const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
-    const int QM = E2 <= 4 ? 16 : 8;
-    const size_t smem2 = scan2_smem_bytes(d, QM, E2);
-
-    // per-level cell hash maps, built on first use
-    struct LevelTab {
-        uint4 *slot = nullptr;
-        uint32_t mask = 0;
-        bool built = false;
-    };
-    LevelTab tabs[MAX_LEVELS];
-    auto build_level = [&](int L) {
-        if (tabs[L].built) return;
-        const int shift = d * L;
-        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
-        scan(flags, rid, n);
-        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
-        uint32_t ncells = read1(small + 0);
-        uint32_t H = 1;
-        while (H < 2 * ncells) H <<= 1;
-        uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
-        CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
-        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
-        tabs[L] = {slot, H - 1, true};
-    };
-
-    // work items of a (level, position)-ordered list of sorted positions
-    auto make_items = [&](const uint32_t *list, int64_t mm, int qpi, uint32_t &nitems) -> uint2 * {
-        uint32_t *gbegin = sc.get<uint32_t>("gbegin", mm + 1);
-        k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(qkeys, list, lvl, mm, d, flags); ++launches;
-        scan(flags, rid, mm);
-        k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
-        CK(cudaMemsetAsync(small + 2, 0, 4, s));
-        uint32_t *skey = sc.get<uint32_t>("skey", mm), *sval = sc.get<uint32_t>("sval", mm);
-        uint32_t *skey2 = sc.get<uint32_t>("skey2", mm), *sval2 = sc.get<uint32_t>("sval2", mm);
-        k_group_sizes<<<grid_for(mm, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
-        fetch(pinned, small + 1, 8);
-        CK(cudaStreamSynchronize(s));
-        uint32_t ng = pinned[0], maxsz = pinned[1];
-        k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
-        radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
-        uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
-        k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
-        scan(nit, ioff, ng);
-        fetch(pinned, ioff + ng - 1, 4);
-        fetch(pinned + 1, nit + ng - 1, 4);
-        CK(cudaStreamSynchronize(s));
-        nitems = pinned[0] + pinned[1];
-        uint2 *items = sc.get<uint2>("items", nitems);
-        k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, list, lvl, items); ++launches;
-        return items;
-    };
-    // entries of `list` whose status is `value`, in order, into `out`
-    auto select_list = [&](const uint32_t *list, int64_t mm, uint32_t value, uint32_t *out) -> int64_t {
-        k_status_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, status, mm, value, flags); ++launches;
-        scan(flags, rid, mm);
-        fetch(pinned, rid + mm - 1, 4);
-        fetch(pinned + 1, flags + mm - 1, 4);
-        CK(cudaStreamSynchronize(s));
-        int64_t cntv = (int64_t)pinned[0] + pinned[1];
-        if (cntv > 0) {
-            k_compact<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, flags, rid, mm, out); ++launches;
-        }
-        return cntv;
-    };
-
+    // Epochs: one under the default policy.  Under the paper's policy each
+    // epoch indexes the data on a grid of cell side eps, runs one pass over
+    // the queries not done yet with the certificate radius capped at eps, and
+    // widens eps by eps_min / 2 (Sec. 4.4 re-indexing; after 256 epochs eps
+    // doubles instead, which bounds the number of epochs).
     int pass = 0;
     int64_t cand_before = 0;
     int first_level = -1;
-    while (m > 0) {
-        if (pass > 4 * MAX_LEVELS) fail(KNN_ERR_CUDA, "internal: too many passes");
-        // order the active list by level (stable: positions stay ordered
-        // within a level) and build the levels' hash maps
-        k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
-        k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
-        k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
-        fetch(pinned, small + 4, 8);
-        CK(cudaStreamSynchronize(s));
-        const uint32_t lmin = pinned[0], lmax = pinned[1];
-        if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
-        if (first_level < 0) first_level = (int)lmin;
-        if (lmin != lmax) {
-            uint32_t *kk = lkey, *kk2 = lkey2;
-            radix_sort<uint32_t>(kk, active, kk2, active2, m, bitlen32(lmax));
+    uint32_t *done = nullptr;  // per original query row (paper's policy)
+    if (policy == 1) {
+        done = sc.get<uint32_t>("done", nq);
+        CK(cudaMemsetAsync(done, 0, sizeof(uint32_t) * nq, s));
+    }
+    float eps_mult = 1.0f;
+    for (int epoch = 0;; ++epoch) {
+        // a3-a5
+        uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
+        uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
+        k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
+        radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
+        float *xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
+        k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
+        // queries: keys on the data grid, sorted, gathered (the data arrays for a self-join)
+        uint64_t *qkeys = keys;
+        uint32_t *qperm = perm;
+        float *qxsort = xsort;
+        if (!self) {
+            uint64_t *ralt = sc.get<uint64_t>("rkeys_alt", nq);
+            uint32_t *rpalt = sc.get<uint32_t>("rperm_alt", nq);
+            qkeys = sc.get<uint64_t>("rkeys", nq);
+            qperm = sc.get<uint32_t>("rperm", nq);
+            k_keys<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, gp, qkeys, qperm); ++launches;
+            radix_sort<uint64_t>(qkeys, qperm, ralt, rpalt, nq, hp.key_bits);
+            qxsort = sc.get<float>("rxsort", (size_t)nq * pad_dim(d));
+            k_gather<<<grid_for(nq, 256, nsm), 256, 0, s>>>(rxs, nq, d, qperm, qxsort); ++launches;
         }
-        for (uint32_t L = lmin; L <= lmax; ++L) build_level((int)L);
+        CK(cudaGetLastError());
+        if (epoch == 0) CK(cudaEventRecord(ev[1], s));
 
-        ScanArgs a;
-        memset(&a, 0, sizeof(a));
-        a.xsort = xsort;
-        a.perm = perm;
-        a.keys = keys;
-        a.qxsort = qxsort;
-        a.qkeys = qkeys;
-        a.qperm = qperm;
-        a.self = self ? 1 : 0;
-        a.counter = small + 3;
-        for (int L = 0; L < MAX_LEVELS; ++L) {
-            a.hslotL[L] = tabs[L].slot;
-            a.hmaskL[L] = tabs[L].mask;
-        }
-        a.fail = status;
-        a.seed = seed;
-        a.out_ids = ids;
-        a.out_dist = dist;
-        a.stats = st;
-        a.n = n;
-        a.K = K;
-        a.bits = hp.bits;
-        for (int k = 0; k < d; ++k) {
-            a.cmax0[k] = hp.cmax0[k];
-            a.lo[k] = hp.lo[k];
-        }
-        a.w0 = hp.w0;
-        a.fixed_ok = hp.fixed_ok;
-        a.F = hp.F;
-        a.B = B1;
-        a.CH = CH;
-        a.noff = noff;
-
-        uint32_t nitems = 0;
-        a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
-        a.active = active;
-        a.nitems = nitems;
-        CK(cudaMemsetAsync(small + 3, 0, 4, s));
-        CK(cudaEventRecord(evs[0], s));
-        if (fast) dispatch_scan2(*this, d, E2, a, smem2);
-        else dispatch_scan(*this, d, a, smem1);
-        CK(cudaEventRecord(evs[1], s));
-        {
-            CK(cudaEventSynchronize(evs[1]));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
-            ms_scan += t;
-            if (pass < 16) stats.ms_pass[pass] = t;
-            fetch(pinned + 8, st, sizeof(unsigned long long));
-            CK(cudaStreamSynchronize(s));
-            unsigned long long c;
-            memcpy(&c, pinned + 8, sizeof(c));
-            if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
-            cand_before = (int64_t)c;
-        }
-        if (fast) {
-            // queries whose buffer overflowed (massive ties): general kernel
-            int64_t mo = select_list(active, m, 2, ovl);
-            if (mo > 0) {
-                a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
-                a.active = ovl;
-                a.nitems = nitems;
-                CK(cudaMemsetAsync(small + 3, 0, 4, s));
-                dispatch_scan(*this, d, a, smem1);
-                stats.overflow_queries += mo;
+        // start level of every query (sliding-window cell counts)
+        uint32_t *lvl = sc.get<uint32_t>("lvl", nq);
+        if (policy == 1) {
+            k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, 0u); ++launches;
+        } else if (!self) {
+            // R x S: every query starts at the search-distance width (queries in
+            // sparse regions move up a level per pass until certified)
+            k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, hp.start_level); ++launches;
+        } else {
+            // target count of a query's parent cell: between the expected counts
+            // of the ideal level's parent and of the ideal level itself
+            const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
+            const double ideal = std::pow(2.0 * (double)wmul, d) * (double)K / Vd;
+            int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
+            if (hp.finer == 0) {
+                // no density skew: every query starts at the search-distance width
+                k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.start_level); ++launches;
+            } else if (n >= H && hp.top_level > 0) {
+                const int64_t nw = n - H + 1;
+                uint8_t *pm = sc.get<uint8_t>("win_pm", nw), *smn = sc.get<uint8_t>("win_sm", nw);
+                const int64_t nblk = (nw + H - 1) / H;
+                k_window_blocks<<<grid_for(nblk, 128, nsm, 16), 128, 0, s>>>(keys, nw, H, d, pm, smn); ++launches;
+                k_start_levels<<<grid_for(n, 256, nsm), 256, 0, s>>>(pm, smn, n, H, hp.top_level, hp.start_level, lvl); ++launches;
+            } else {
+                k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.top_level); ++launches;
             }
         }
-        k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
-        int64_t next = select_list(active, m, 1, active2);
-        if (pass < 16) stats.pass_queries[pass] = m;
-        std::swap(active, active2);
-        m = next;
-        ++pass;
+
+        // pass loop
+        // query-side arrays are indexed by sorted query position
+        const int64_t nmax = std::max(n, nq);
+        uint32_t *active = sc.get<uint32_t>("active", nq), *active2 = sc.get<uint32_t>("active2", nq);
+        uint32_t *ovl = sc.get<uint32_t>("ovl", nq);
+        uint32_t *flags = sc.get<uint32_t>("flags", nmax), *rid = sc.get<uint32_t>("rid", nmax);
+        uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
+        uint32_t *small = sc.get<uint32_t>("small", 16);
+        uint32_t *status = sc.get<uint32_t>("fail", nq);  // per sorted query position
+        float *seed = sc.get<float>("seed", nq);           // per sorted query position, +inf to start
+        k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>((uint32_t *)seed, nq, 0x7f800000u); ++launches;
+        uint32_t *lkey = sc.get<uint32_t>("lkey", nq), *lkey2 = sc.get<uint32_t>("lkey2", nq);
+        k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
+        int64_t m = nq;
+        if (policy == 1 && epoch > 0) {
+            // the queries not done yet, by their position in this epoch's order
+            k_undone_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, done, nq, flags); ++launches;
+            scan(flags, rid, nq);
+            fetch(pinned, rid + nq - 1, 4);
+            fetch(pinned + 1, flags + nq - 1, 4);
+            CK(cudaStreamSynchronize(s));
+            m = (int64_t)pinned[0] + pinned[1];
+            k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
+            std::swap(active, active2);
+        }
+        // general kernel (scan.cuh)
+        const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
+        const int CH = d <= 6 ? 1024 : 512;
+        int noff = 1;
+        for (int k = 0; k < d; ++k) noff *= 3;
+        const size_t smem1 = scan_smem_bytes(d, noff, CH, B1);
+        // fast kernel (scan2.cuh)
+        const bool fast = K + 32 <= 256;
+        const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
+        const int QM = E2 <= 4 ? 16 : 8;
+        const size_t smem2 = scan2_smem_bytes(d, QM, E2);
+
+        // per-level cell hash maps, built on first use
+        struct LevelTab {
+            uint4 *slot = nullptr;
+            uint32_t mask = 0;
+            bool built = false;
+        };
+        LevelTab tabs[MAX_LEVELS];
+        auto build_level = [&](int L) {
+            if (tabs[L].built) return;
+            const int shift = d * L;
+            k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
+            scan(flags, rid, n);
+            k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
+            uint32_t ncells = read1(small + 0);
+            uint32_t H = 1;
+            while (H < 2 * ncells) H <<= 1;
+            uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
+            CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
+            k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
+            tabs[L] = {slot, H - 1, true};
+        };
+
+        // work items of a (level, position)-ordered list of sorted positions
+        auto make_items = [&](const uint32_t *list, int64_t mm, int qpi, uint32_t &nitems) -> uint2 * {
+            uint32_t *gbegin = sc.get<uint32_t>("gbegin", mm + 1);
+            k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(qkeys, list, lvl, mm, d, flags); ++launches;
+            scan(flags, rid, mm);
+            k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
+            CK(cudaMemsetAsync(small + 2, 0, 4, s));
+            uint32_t *skey = sc.get<uint32_t>("skey", mm), *sval = sc.get<uint32_t>("sval", mm);
+            uint32_t *skey2 = sc.get<uint32_t>("skey2", mm), *sval2 = sc.get<uint32_t>("sval2", mm);
+            k_group_sizes<<<grid_for(mm, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
+            fetch(pinned, small + 1, 8);
+            CK(cudaStreamSynchronize(s));
+            uint32_t ng = pinned[0], maxsz = pinned[1];
+            k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
+            radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+            uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
+            k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
+            scan(nit, ioff, ng);
+            fetch(pinned, ioff + ng - 1, 4);
+            fetch(pinned + 1, nit + ng - 1, 4);
+            CK(cudaStreamSynchronize(s));
+            nitems = pinned[0] + pinned[1];
+            uint2 *items = sc.get<uint2>("items", nitems);
+            k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, list, lvl, items); ++launches;
+            return items;
+        };
+        // entries of `list` whose status is `value`, in order, into `out`
+        auto select_list = [&](const uint32_t *list, int64_t mm, uint32_t value, uint32_t *out) -> int64_t {
+            k_status_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, status, mm, value, flags); ++launches;
+            scan(flags, rid, mm);
+            fetch(pinned, rid + mm - 1, 4);
+            fetch(pinned + 1, flags + mm - 1, 4);
+            CK(cudaStreamSynchronize(s));
+            int64_t cntv = (int64_t)pinned[0] + pinned[1];
+            if (cntv > 0) {
+                k_compact<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, flags, rid, mm, out); ++launches;
+            }
+            return cntv;
+        };
+
+        while (m > 0) {
+            if (pass > (policy == 1 ? 8192 : 4 * MAX_LEVELS)) fail(KNN_ERR_CUDA, "internal: too many passes");
+            // order the active list by level (stable: positions stay ordered
+            // within a level) and build the levels' hash maps
+            k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
+            k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
+            k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
+            fetch(pinned, small + 4, 8);
+            CK(cudaStreamSynchronize(s));
+            const uint32_t lmin = pinned[0], lmax = pinned[1];
+            if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
+            if (first_level < 0) first_level = (int)lmin;
+            if (lmin != lmax) {
+                uint32_t *kk = lkey, *kk2 = lkey2;
+                radix_sort<uint32_t>(kk, active, kk2, active2, m, bitlen32(lmax));
+            }
+            for (uint32_t L = lmin; L <= lmax; ++L) build_level((int)L);
+
+            ScanArgs a;
+            memset(&a, 0, sizeof(a));
+            a.xsort = xsort;
+            a.perm = perm;
+            a.keys = keys;
+            a.qxsort = qxsort;
+            a.qkeys = qkeys;
+            a.qperm = qperm;
+            a.self = self ? 1 : 0;
+            a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
+            a.counter = small + 3;
+            for (int L = 0; L < MAX_LEVELS; ++L) {
+                a.hslotL[L] = tabs[L].slot;
+                a.hmaskL[L] = tabs[L].mask;
+            }
+            a.fail = status;
+            a.seed = seed;
+            a.out_ids = ids;
+            a.out_dist = dist;
+            a.stats = st;
+            a.n = n;
+            a.K = K;
+            a.bits = hp.bits;
+            for (int k = 0; k < d; ++k) {
+                a.cmax0[k] = hp.cmax0[k];
+                a.lo[k] = hp.lo[k];
+            }
+            a.w0 = hp.w0;
+            a.fixed_ok = hp.fixed_ok;
+            a.F = hp.F;
+            a.B = B1;
+            a.CH = CH;
+            a.noff = noff;
+
+            uint32_t nitems = 0;
+            a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
+            a.active = active;
+            a.nitems = nitems;
+            CK(cudaMemsetAsync(small + 3, 0, 4, s));
+            CK(cudaEventRecord(evs[0], s));
+            if (fast) dispatch_scan2(*this, d, E2, a, smem2);
+            else dispatch_scan(*this, d, a, smem1);
+            CK(cudaEventRecord(evs[1], s));
+            {
+                CK(cudaEventSynchronize(evs[1]));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
+                ms_scan += t;
+                if (pass < 16) stats.ms_pass[pass] = t;
+                fetch(pinned + 8, st, sizeof(unsigned long long));
+                CK(cudaStreamSynchronize(s));
+                unsigned long long c;
+                memcpy(&c, pinned + 8, sizeof(c));
+                if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
+                cand_before = (int64_t)c;
+            }
+            if (fast) {
+                // queries whose buffer overflowed (massive ties): general kernel
+                int64_t mo = select_list(active, m, 2, ovl);
+                if (mo > 0) {
+                    a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
+                    a.active = ovl;
+                    a.nitems = nitems;
+                    CK(cudaMemsetAsync(small + 3, 0, 4, s));
+                    dispatch_scan(*this, d, a, smem1);
+                    stats.overflow_queries += mo;
+                }
+            }
+            if (policy == 1) {
+                k_mark_done<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, qperm, done); ++launches;
+                int64_t left = select_list(active, m, 1, active2);
+                if (pass < 16) stats.pass_queries[pass] = m;
+                ++pass;
+                m = left;
+                break;  // next epoch (or done)
+            }
+            k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
+            int64_t next = select_list(active, m, 1, active2);
+            if (pass < 16) stats.pass_queries[pass] = m;
+            std::swap(active, active2);
+            m = next;
+            ++pass;
+        }
+        if (policy != 1 || m == 0) break;
+        // re-index: eps += eps_min / 2 (doubling after 256 epochs)
+        eps_mult = epoch < 256 ? eps_mult + 0.5f : eps_mult * 2.0f;
+        pin.width_mult = eps_mult;
+        k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
+        hp = read1(gp);
     }
     stats.start_level = first_level;
     stats.passes = pass;
@@ -974,6 +1021,7 @@ static void start_workers(knnjoin_ctx *ctx)
         w->pipe.big_token = &ctx->big_token;
         w->pipe.width_mult = ctx->main.width_mult;
         w->pipe.tune = &ctx->tune;
+        w->pipe.policy = ctx->main.policy;
         ctx->workers.push_back(std::move(w));
     }
     for (auto &w : ctx->workers) {
@@ -1060,6 +1108,8 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
         if (ctx->cfg.tune_cache_path) ctx->tune.path = ctx->cfg.tune_cache_path;
         ctx->tune.load();
         ctx->main.tune = &ctx->tune;
+        if (ctx->cfg.policy < 0 || ctx->cfg.policy > 1) fail(KNN_ERR_INVALID, "policy must be 0 or 1");
+        ctx->main.policy = ctx->cfg.policy;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
         if (ctx->cfg.workers > 0) ctx->nworkers = std::min(ctx->cfg.workers, 64);
         size_t freeb = 0, totalb = 0;

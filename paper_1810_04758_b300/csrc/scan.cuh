@@ -63,6 +63,7 @@ struct ScanArgs {
     const uint64_t *qkeys;     // sorted query keys on the data grid
     const uint32_t *qperm;     // query key order -> original query row
     int self;                  // 1: self-join (a query's own point is not its neighbour)
+    float rcap;                // > 0: certificate radius capped at this (the paper's policy)
     int CH;                    // staged candidates per chunk
     int noff;                  // 3^d
 };
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                     R = fminf(R, __fsub_rd(f, q[k]));
                 }
             }
+            if (a.rcap > 0.0f) R = fminf(R, a.rcap);  // the paper's policy: K within eps
             if (m >= K) {
                 if (isinf(R)) {
                     certified = true;

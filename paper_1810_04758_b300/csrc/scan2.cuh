@@ -421,7 +421,7 @@ __device__ __forceinline__ float cert_radius(const float *q, const int *cell, co
         if (cL >= 2) R = fminf(R, __fsub_rd(q[k], face_of((cL - 1) << level, a.lo[k], a.w0)));
         if (cL + 1 < cmaxL[k]) R = fminf(R, __fsub_rd(face_of((cL + 2) << level, a.lo[k], a.w0), q[k]));
     }
-    return R;
+    return a.rcap > 0.0f ? fminf(R, a.rcap) : R;  // the paper's policy: K within eps
 }
 
 // Buffer full: find its K-th value T, lower the threshold to the band of T
