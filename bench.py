@@ -114,6 +114,17 @@ def profiled_traffic(workload: str):
     return int(m.group(1))
 
 
+def tune_cache_keys(path: str) -> set:
+    """(d, K, floor(log2 n)) keys already in a knnjoin tune cache file."""
+    if not path or not os.path.exists(path):
+        return set()
+    try:
+        with open(path) as f:
+            return {(e["d"], e["K"], e["nlog2"]) for e in json.load(f)["entries"]}
+    except (OSError, ValueError, KeyError):
+        return set()
+
+
 def wref_table():
     try:
         with open(os.path.join(ROOT, "tests", "golden", "wref_2m.json")) as f:
@@ -285,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    ctx = kj.Context(device=local_rank, stream=stream, policy=args.policy)
+    ctx = kj.Context(device=local_rank, stream=stream, policy=args.policy,
+                     tune_cache_path=args.tune_cache or None)
     names = WORKLOADS[args.workload]
     if args.configs:
         names = [nm for nm in names if nm in args.configs.split(",")]
@@ -299,8 +311,13 @@ def run_ours(args, rank, world, local_rank):
     # the join at several multipliers and keeps the fastest per (d, K, log2 n)
     tuned = {}
     if not args.no_autotune and args.policy == 0:
+        cached = tune_cache_keys(args.tune_cache)
         for nm in names:
-            tuned[nm] = ctx.autotune(dpts[nm], hosts[nm][1])
+            n_, d_ = hosts[nm][0].shape
+            if (d_, hosts[nm][1], int(n_).bit_length() - 1) in cached:
+                tuned[nm] = "cached"
+            else:
+                tuned[nm] = ctx.autotune(dpts[nm], hosts[nm][1])
         torch.cuda.synchronize()
 
     def one_step(collect):
@@ -745,6 +762,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--policy", type=int, choices=[0, 1], default=0,
                     help="1: the paper's GPU-Only policy (global eps, re-index eps += eps_min/2)")
+    ap.add_argument("--tune-cache", default="",
+                    help="tune cache file (JSON): joins already in it are not re-tuned")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default cell-width multiplier instead of autotuning it first")
     ap.add_argument("--configs", default="",
