@@ -81,7 +81,11 @@ typedef struct {
                                  when fewer than K neighbours lie within eps, and failed queries
                                  are redone on a grid re-indexed with eps += eps_min / 2.
                                  Results are identical; speed differs */
-    int reserved[6];
+    int out_chunk_mb;         /* results bound for host memory are computed in chunks of
+                                 query rows whose device output is at most this many MiB,
+                                 each copied out before the next (0 = only when the results
+                                 exceed half of the free device memory) */
+    int reserved[5];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */
@@ -117,6 +121,7 @@ typedef struct {
     double ms_pass[16];            /* device time of each pass's scan launches */
     int64_t pass_candidates[16];   /* candidate distance evaluations of each pass */
     double width_mult;             /* cell-width multiplier the join used */
+    int64_t chunks;                /* output chunks (1 unless out_chunk_mb applied) */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).

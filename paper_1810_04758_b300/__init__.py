@@ -41,8 +41,8 @@ class KnnjoinConfig(ctypes.Structure):
                 ("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("user", ctypes.c_void_p),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
                 ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
-                ("workers", ctypes.c_int), ("policy", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("workers", ctypes.c_int), ("policy", ctypes.c_int), ("out_chunk_mb", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class KnnjoinJob(ctypes.Structure):
@@ -63,7 +63,8 @@ class KnnjoinStats(ctypes.Structure):
                 ("ms_wall", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16),
                 ("pass_candidates", ctypes.c_int64 * 16),
-                ("width_mult", ctypes.c_double)]
+                ("width_mult", ctypes.c_double),
+                ("chunks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -220,7 +221,7 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
                  max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0,
-                 tune_cache_path: Optional[str] = None, policy: int = 0):
+                 tune_cache_path: Optional[str] = None, policy: int = 0, out_chunk_mb: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -237,6 +238,7 @@ class Context:
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.workers = workers
         cfg.policy = policy
+        cfg.out_chunk_mb = out_chunk_mb
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None
         cfg.tune_cache_path = self._tune_path
         self._cfg = cfg

@@ -628,6 +628,17 @@ __global__ void k_mark_done(const uint32_t *__restrict__ list, const uint32_t *_
     }
 }
 
+// Chunked output: flag the sorted query positions whose original row lies in
+// [r0, r1).
+__global__ void k_row_flags(const uint32_t *__restrict__ qperm, int64_t nq, uint32_t r0, uint32_t r1,
+                            uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nq; a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = qperm[a];
+        flags[a] = r >= r0 && r < r1;
+    }
+}
+
 // Small readback: copy `words` 32-bit words (to mapped host memory).
 __global__ void k_fetch(uint32_t *dst, const uint32_t *__restrict__ src, int words)
 {

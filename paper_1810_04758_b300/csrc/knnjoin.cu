@@ -221,6 +221,7 @@ struct Pipeline {
     TuneTable *tune = nullptr;
     float force_wm = 0.0f;         // > 0: this multiplier (autotuning runs)
     int policy = 0;                // knnjoin_config.policy
+    size_t out_chunk_bytes = 0;    // knnjoin_config.out_chunk_mb (0: automatic)
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
@@ -491,8 +492,25 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             qry = p;
         }
     }
-    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)nq * K);
-    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)nq * K);
+    // results bound for host memory that would not fit on the device (or
+    // exceed out_chunk_bytes) are computed in chunks of query rows, each
+    // copied out before the next
+    int64_t chunk_rows = nq;
+    if (policy == 0 && !(ids_dev && dist_dev)) {
+        const size_t row_bytes = (size_t)K * (sizeof(int32_t) + sizeof(double));
+        size_t limit = out_chunk_bytes;
+        if (limit == 0) {
+            size_t freeb = 0, totalb = 0;
+            CK(cudaMemGetInfo(&freeb, &totalb));
+            if ((size_t)nq * row_bytes > freeb / 2) limit = freeb / 4;
+        }
+        if (limit > 0 && (size_t)nq * row_bytes > limit)
+            chunk_rows = std::max<int64_t>(1, (int64_t)(limit / row_bytes));
+    }
+    const bool chunked = chunk_rows < nq;
+    stats.chunks = (nq + chunk_rows - 1) / chunk_rows;
+    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)chunk_rows * K);
+    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)chunk_rows * K);
     CK(cudaEventRecord(ev[0], s));
 
     // a1
@@ -631,19 +649,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         float *seed = sc.get<float>("seed", nq);           // per sorted query position, +inf to start
         k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>((uint32_t *)seed, nq, 0x7f800000u); ++launches;
         uint32_t *lkey = sc.get<uint32_t>("lkey", nq), *lkey2 = sc.get<uint32_t>("lkey2", nq);
-        k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
-        int64_t m = nq;
-        if (policy == 1 && epoch > 0) {
-            // the queries not done yet, by their position in this epoch's order
-            k_undone_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, done, nq, flags); ++launches;
-            scan(flags, rid, nq);
-            fetch(pinned, rid + nq - 1, 4);
-            fetch(pinned + 1, flags + nq - 1, 4);
-            CK(cudaStreamSynchronize(s));
-            m = (int64_t)pinned[0] + pinned[1];
-            k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
-            std::swap(active, active2);
-        }
+        int64_t m = 0, row0 = 0;
         // general kernel (scan.cuh)
         const int B1 = std::max(128, 1 << bitlen32((uint32_t)(2 * K - 1)));
         const int CH = d <= 6 ? 1024 : 512;
@@ -718,106 +724,141 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             return cntv;
         };
 
-        while (m > 0) {
-            if (pass > (policy == 1 ? 8192 : 4 * MAX_LEVELS)) fail(KNN_ERR_CUDA, "internal: too many passes");
-            // order the active list by level (stable: positions stay ordered
-            // within a level) and build the levels' hash maps
-            k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
-            k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
-            k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
-            fetch(pinned, small + 4, 8);
-            CK(cudaStreamSynchronize(s));
-            const uint32_t lmin = pinned[0], lmax = pinned[1];
-            if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
-            if (first_level < 0) first_level = (int)lmin;
-            if (lmin != lmax) {
-                uint32_t *kk = lkey, *kk2 = lkey2;
-                radix_sort<uint32_t>(kk, active, kk2, active2, m, bitlen32(lmax));
-            }
-            for (uint32_t L = lmin; L <= lmax; ++L) build_level((int)L);
-
-            ScanArgs a;
-            memset(&a, 0, sizeof(a));
-            a.xsort = xsort;
-            a.perm = perm;
-            a.keys = keys;
-            a.qxsort = qxsort;
-            a.qkeys = qkeys;
-            a.qperm = qperm;
-            a.self = self ? 1 : 0;
-            a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
-            a.counter = small + 3;
-            for (int L = 0; L < MAX_LEVELS; ++L) {
-                a.hslotL[L] = tabs[L].slot;
-                a.hmaskL[L] = tabs[L].mask;
-            }
-            a.fail = status;
-            a.seed = seed;
-            a.out_ids = ids;
-            a.out_dist = dist;
-            a.stats = st;
-            a.n = n;
-            a.K = K;
-            a.bits = hp.bits;
-            for (int k = 0; k < d; ++k) {
-                a.cmax0[k] = hp.cmax0[k];
-                a.lo[k] = hp.lo[k];
-            }
-            a.w0 = hp.w0;
-            a.fixed_ok = hp.fixed_ok;
-            a.F = hp.F;
-            a.B = B1;
-            a.CH = CH;
-            a.noff = noff;
-
-            uint32_t nitems = 0;
-            a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
-            a.active = active;
-            a.nitems = nitems;
-            CK(cudaMemsetAsync(small + 3, 0, 4, s));
-            CK(cudaEventRecord(evs[0], s));
-            if (fast) dispatch_scan2(*this, d, E2, a, smem2);
-            else dispatch_scan(*this, d, a, smem1);
-            CK(cudaEventRecord(evs[1], s));
-            {
-                CK(cudaEventSynchronize(evs[1]));
-                float t = 0.f;
-                CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
-                ms_scan += t;
-                if (pass < 16) stats.ms_pass[pass] = t;
-                fetch(pinned + 8, st, sizeof(unsigned long long));
+        for (int64_t r0 = 0; r0 < nq; r0 += chunk_rows) {
+            const int64_t r1 = std::min(nq, r0 + chunk_rows);
+            k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
+            m = nq;
+            if (policy == 1 && epoch > 0) {
+                // the queries not done yet, by their position in this epoch's order
+                k_undone_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, done, nq, flags); ++launches;
+                scan(flags, rid, nq);
+                fetch(pinned, rid + nq - 1, 4);
+                fetch(pinned + 1, flags + nq - 1, 4);
                 CK(cudaStreamSynchronize(s));
-                unsigned long long c;
-                memcpy(&c, pinned + 8, sizeof(c));
-                if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
-                cand_before = (int64_t)c;
+                m = (int64_t)pinned[0] + pinned[1];
+                k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
+                std::swap(active, active2);
             }
-            if (fast) {
-                // queries whose buffer overflowed (massive ties): general kernel
-                int64_t mo = select_list(active, m, 2, ovl);
-                if (mo > 0) {
-                    a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
-                    a.active = ovl;
-                    a.nitems = nitems;
-                    CK(cudaMemsetAsync(small + 3, 0, 4, s));
-                    dispatch_scan(*this, d, a, smem1);
-                    stats.overflow_queries += mo;
+            if (chunked) {
+                // this chunk's queries: original rows [r0, r1)
+                k_row_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, nq, (uint32_t)r0, (uint32_t)r1, flags); ++launches;
+                scan(flags, rid, nq);
+                fetch(pinned, rid + nq - 1, 4);
+                fetch(pinned + 1, flags + nq - 1, 4);
+                CK(cudaStreamSynchronize(s));
+                m = (int64_t)pinned[0] + pinned[1];
+                k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
+                std::swap(active, active2);
+            }
+            row0 = r0;
+            while (m > 0) {
+                if (pass > (policy == 1 ? 8192 : 4 * MAX_LEVELS)) fail(KNN_ERR_CUDA, "internal: too many passes");
+                // order the active list by level (stable: positions stay ordered
+                // within a level) and build the levels' hash maps
+                k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
+                k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
+                k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
+                fetch(pinned, small + 4, 8);
+                CK(cudaStreamSynchronize(s));
+                const uint32_t lmin = pinned[0], lmax = pinned[1];
+                if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
+                if (first_level < 0) first_level = (int)lmin;
+                if (lmin != lmax) {
+                    uint32_t *kk = lkey, *kk2 = lkey2;
+                    radix_sort<uint32_t>(kk, active, kk2, active2, m, bitlen32(lmax));
                 }
-            }
-            if (policy == 1) {
-                k_mark_done<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, qperm, done); ++launches;
-                int64_t left = select_list(active, m, 1, active2);
+                for (uint32_t L = lmin; L <= lmax; ++L) build_level((int)L);
+
+                ScanArgs a;
+                memset(&a, 0, sizeof(a));
+                a.xsort = xsort;
+                a.perm = perm;
+                a.keys = keys;
+                a.qxsort = qxsort;
+                a.qkeys = qkeys;
+                a.qperm = qperm;
+                a.self = self ? 1 : 0;
+                a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
+            a.row0 = row0;
+                a.counter = small + 3;
+                for (int L = 0; L < MAX_LEVELS; ++L) {
+                    a.hslotL[L] = tabs[L].slot;
+                    a.hmaskL[L] = tabs[L].mask;
+                }
+                a.fail = status;
+                a.seed = seed;
+                a.out_ids = ids;
+                a.out_dist = dist;
+                a.stats = st;
+                a.n = n;
+                a.K = K;
+                a.bits = hp.bits;
+                for (int k = 0; k < d; ++k) {
+                    a.cmax0[k] = hp.cmax0[k];
+                    a.lo[k] = hp.lo[k];
+                }
+                a.w0 = hp.w0;
+                a.fixed_ok = hp.fixed_ok;
+                a.F = hp.F;
+                a.B = B1;
+                a.CH = CH;
+                a.noff = noff;
+
+                uint32_t nitems = 0;
+                a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
+                a.active = active;
+                a.nitems = nitems;
+                CK(cudaMemsetAsync(small + 3, 0, 4, s));
+                CK(cudaEventRecord(evs[0], s));
+                if (fast) dispatch_scan2(*this, d, E2, a, smem2);
+                else dispatch_scan(*this, d, a, smem1);
+                CK(cudaEventRecord(evs[1], s));
+                {
+                    CK(cudaEventSynchronize(evs[1]));
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
+                    ms_scan += t;
+                    if (pass < 16) stats.ms_pass[pass] = t;
+                    fetch(pinned + 8, st, sizeof(unsigned long long));
+                    CK(cudaStreamSynchronize(s));
+                    unsigned long long c;
+                    memcpy(&c, pinned + 8, sizeof(c));
+                    if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
+                    cand_before = (int64_t)c;
+                }
+                if (fast) {
+                    // queries whose buffer overflowed (massive ties): general kernel
+                    int64_t mo = select_list(active, m, 2, ovl);
+                    if (mo > 0) {
+                        a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
+                        a.active = ovl;
+                        a.nitems = nitems;
+                        CK(cudaMemsetAsync(small + 3, 0, 4, s));
+                        dispatch_scan(*this, d, a, smem1);
+                        stats.overflow_queries += mo;
+                    }
+                }
+                if (policy == 1) {
+                    k_mark_done<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, qperm, done); ++launches;
+                    int64_t left = select_list(active, m, 1, active2);
+                    if (pass < 16) stats.pass_queries[pass] = m;
+                    ++pass;
+                    m = left;
+                    break;  // next epoch (or done)
+                }
+                k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
+                int64_t next = select_list(active, m, 1, active2);
                 if (pass < 16) stats.pass_queries[pass] = m;
+                std::swap(active, active2);
+                m = next;
                 ++pass;
-                m = left;
-                break;  // next epoch (or done)
             }
-            k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
-            int64_t next = select_list(active, m, 1, active2);
-            if (pass < 16) stats.pass_queries[pass] = m;
-            std::swap(active, active2);
-            m = next;
-            ++pass;
+            if (chunked) {
+                const int64_t rows = r1 - r0;
+                k_sqrt_rows<<<grid_for(rows * K, 256, nsm, 16), 256, 0, s>>>(dist, rows * K); ++launches;
+                CK(cudaMemcpyAsync(ids_in + r0 * K, ids, sizeof(int32_t) * rows * K, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(dist_in + r0 * K, dist, sizeof(double) * rows * K, cudaMemcpyDeviceToHost, s));
+            }
         }
         if (policy != 1 || m == 0) break;
         // re-index: eps += eps_min / 2 (doubling after 256 epochs)
@@ -828,14 +869,16 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     }
     stats.start_level = first_level;
     stats.passes = pass;
-    k_sqrt_rows<<<grid_for(nq * K, 256, nsm, 16), 256, 0, s>>>(dist, nq * K); ++launches;
+    if (!chunked) {
+        k_sqrt_rows<<<grid_for(nq * K, 256, nsm, 16), 256, 0, s>>>(dist, nq * K); ++launches;
+    }
     CK(cudaEventRecord(ev[2], s));
     if (turn.owns_lock()) {
         CK(cudaEventSynchronize(ev[2]));
         turn.unlock();
     }
-    if (!ids_dev) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s));
-    if (!dist_dev) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * nq * K, cudaMemcpyDeviceToHost, s));
+    if (!ids_dev && !chunked) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s));
+    if (!dist_dev && !chunked) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * nq * K, cudaMemcpyDeviceToHost, s));
     fetch(pinned, st, 4 * sizeof(unsigned long long));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
@@ -1022,6 +1065,7 @@ static void start_workers(knnjoin_ctx *ctx)
         w->pipe.width_mult = ctx->main.width_mult;
         w->pipe.tune = &ctx->tune;
         w->pipe.policy = ctx->main.policy;
+        w->pipe.out_chunk_bytes = ctx->main.out_chunk_bytes;
         ctx->workers.push_back(std::move(w));
     }
     for (auto &w : ctx->workers) {
@@ -1110,6 +1154,8 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
         ctx->main.tune = &ctx->tune;
         if (ctx->cfg.policy < 0 || ctx->cfg.policy > 1) fail(KNN_ERR_INVALID, "policy must be 0 or 1");
         ctx->main.policy = ctx->cfg.policy;
+        if (ctx->cfg.out_chunk_mb < 0) fail(KNN_ERR_INVALID, "out_chunk_mb must be >= 0");
+        ctx->main.out_chunk_bytes = (size_t)ctx->cfg.out_chunk_mb << 20;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
         if (ctx->cfg.workers > 0) ctx->nworkers = std::min(ctx->cfg.workers, 64);
         size_t freeb = 0, totalb = 0;

@@ -64,6 +64,7 @@ struct ScanArgs {
     const uint32_t *qperm;     // query key order -> original query row
     int self;                  // 1: self-join (a query's own point is not its neighbour)
     float rcap;                // > 0: certificate radius capped at this (the paper's policy)
+    int64_t row0;              // first output row held by out_ids/out_dist (chunked output)
     int CH;                    // staged candidates per chunk
     int noff;                  // 3^d
 };
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 }
             }
             if (certified) {
-                const int64_t row = (int64_t)a.qperm[qs] * K;
+                const int64_t row = ((int64_t)a.qperm[qs] - a.row0) * K;
                 for (int u = 0; u < mine; ++u)
                     if (rr[u] < (uint32_t)K) {
                         a.out_ids[row + rr[u]] = (int32_t)rid[u];

@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
                 if (certified) {
                     flag = 0;
-                    const int64_t row = (int64_t)a.qperm[qsv[i]] * K;
+                    const int64_t row = ((int64_t)a.qperm[qsv[i]] - a.row0) * K;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int g = lane * E + e;

@@ -8,8 +8,9 @@ int main(void)
     printf("config %zu %zu %zu %zu\n", sizeof(knnjoin_config), offsetof(knnjoin_config, width_mult),
            offsetof(knnjoin_config, hbm_budget_bytes), offsetof(knnjoin_config, workers));
     printf("job %zu %zu\n", sizeof(knnjoin_job), offsetof(knnjoin_job, out_dist));
-    printf("stats %zu %zu %zu %zu %zu %zu %zu\n", sizeof(knnjoin_stats), offsetof(knnjoin_stats, candidates),
+    printf("stats %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(knnjoin_stats), offsetof(knnjoin_stats, candidates),
            offsetof(knnjoin_stats, ms_index), offsetof(knnjoin_stats, ms_wall), offsetof(knnjoin_stats, ms_pass),
-           offsetof(knnjoin_stats, pass_candidates), offsetof(knnjoin_stats, width_mult));
+           offsetof(knnjoin_stats, pass_candidates), offsetof(knnjoin_stats, width_mult),
+           offsetof(knnjoin_stats, chunks));
     return 0;
 }
