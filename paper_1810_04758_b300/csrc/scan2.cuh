@@ -2,26 +2,35 @@
 // (paper Alg. 1 GPUJoinKernel, Sec. 4.7, GPU: Optimizing Task Granularity), the fast path.
 //
 // Each warp works alone (no block barriers) on work items of up to QM
-// queries that share a level-l grid cell:
-//   a7  lanes look up the 3^d neighbouring cells, 32 at a time, in the
-//       level's hash map, and a warp prefix sum flattens their point runs;
-//   a8  lane t takes candidate t of the flattened runs, loads its
-//       coordinates once (one or two aligned vector loads through L1/L2) and
-//       scores it against every query of the item (query coordinates are
-//       broadcast from shared memory), so a candidate read serves QM queries.
-//       A candidate is kept only if its FP32 squared distance is at most the
-//       query's threshold, which starts at R^2 (1 + 2^-14) -- R the distance
-//       from the query to the faces of the scanned box, the certificate
-//       radius: a point farther than R cannot belong to a certified answer
-//       -- and drops to T (1 + 2^-15) + 2^-120 when the per-query buffer of B
-//       entries fills (T = its K-th value, found by a warp radix select);
-//   a9  per query, the warp selects T32 (the K-th FP32 value), keeps the band
-//       d2_32 <= T32 (1 + 2^-15) + 2^-120, scores the band with the bit-exact
-//       canonical FP64 distance (exact.cuh), sorts it by (D, original id)
-//       with a warp bitonic network and certifies the K-th against R;
+// queries that share a level-l grid cell.  Per batch of 32 neighbour cells,
+// nearest first:
+//   a7  each lane forms its cell's level key from the item's table of
+//       dilated coordinate parts, probes the level's hash map (one 16-byte
+//       load per probe) and, for every query of the item, tests the cell's
+//       box against the query's threshold with a rounded-down squared
+//       distance (a bit per query: the cell mask); a warp prefix sum
+//       flattens the runs;
+//   a8  runs of at least S2_BIG points go first, in super-tiles of S2_SUPER
+//       consecutive sorted points, each tested per query against the box of
+//       its Morton prefix; the other runs are scanned two tiles at a time:
+//       lane t holds candidates t and t + 32, loads their coordinates once
+//       and scores them against every query in the tiles' masks (query rows
+//       broadcast from shared memory), so a candidate read serves up to QM
+//       queries.  A candidate is kept when its FP32 squared distance is at
+//       most the query's threshold: R^2 (1 + 2^-14) to start -- R the
+//       distance to the faces of the scanned box, beyond which no point can
+//       belong to a certified answer -- or the band of the K-th value an
+//       earlier pass found, and T (1 + 2^-15) + 2^-120 once the per-query
+//       buffer of B entries has filled (T = its K-th value, by a warp radix
+//       select);
+//   a9  per query, the warp sorts the buffer as 32-bit keys, takes T32 (the
+//       K-th FP32 value), keeps the band d2_32 <= T32 (1 + 2^-15) + 2^-120,
+//       scores it with the bit-exact canonical FP64 distance (exact.cuh),
+//       orders it by (D, original id) and certifies the K-th against R;
 //   a10 writes the per-point status: 0 certified, 1 not certified (fewer
-//       than K points within R, or D_K >= R^2: retry one level up), 2 buffer
-//       overflow (massive ties: redone by the general kernel of scan.cuh);
+//       than K points within R, or D_K >= R^2: retry one level up, starting
+//       from the band of this K-th value), 2 buffer overflow (massive ties:
+//       redone by the general kernel of scan.cuh);
 //   a11 writes certified rows: original ids and the bit patterns of D (the
 //       correctly rounded square roots are taken afterwards, k_sqrt_rows).
 #pragma once
@@ -265,43 +274,6 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&D)[E], uint32_t (&I)[E],
                         D[e] = od;
                         I[e] = oi;
                     }
-                }
-            }
-        }
-    }
-}
-
-// Bitonic sort, ascending, of 32*E 64-bit values held E per lane in blocked
-// order (entry g = lane*E + e).
-template <int E>
-__device__ __forceinline__ void warp_bitonic_u64(uint64_t (&V)[E], int lane)
-{
-    constexpr int N = 32 * E;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < E) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int p = e ^ j;
-                    if (p > e) {
-                        const bool up = ((lane * E + e) & k) == 0;
-                        const uint64_t lo = V[e] < V[p] ? V[e] : V[p];
-                        const uint64_t hi = V[e] < V[p] ? V[p] : V[e];
-                        V[e] = up ? lo : hi;
-                        V[p] = up ? hi : lo;
-                    }
-                }
-            } else {
-                const int lm = j / E;
-                const bool lower = (lane & lm) == 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const uint64_t o = __shfl_xor_sync(FULL, V[e], lm);
-                    const bool up = ((lane * E + e) & k) == 0;
-                    const bool keep_min = lower == up;
-                    V[e] = keep_min ? (o < V[e] ? o : V[e]) : (o < V[e] ? V[e] : o);
                 }
             }
         }
