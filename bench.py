@@ -430,11 +430,13 @@ def run_ours(args, rank, world, local_rank):
         hout = {nm: (torch.empty((len(hosts[nm][0]), hosts[nm][1]), dtype=torch.int32).pin_memory(),
                      torch.empty((len(hosts[nm][0]), hosts[nm][1]), dtype=torch.float64).pin_memory())
                 for nm in names}
-        # steps through knnjoin_submit / knnjoin_poll, two steps in flight: the
+        # steps through knnjoin_submit / knnjoin_poll, several steps in flight: the
         # worker pool runs each join on its own stream, so a step's result
         # copies overlap the next step's kernels (output buffers alternate)
-        hout2 = [hout, {nm: (torch.empty_like(hout[nm][0]).pin_memory(),
-                             torch.empty_like(hout[nm][1]).pin_memory()) for nm in names}]
+        depth = max(1, args.e2e_depth)
+        hout2 = [hout] + [{nm: (torch.empty_like(hout[nm][0]).pin_memory(),
+                                torch.empty_like(hout[nm][1]).pin_memory()) for nm in names}
+                          for _ in range(depth - 1)]
 
         def wait(jid):
             while True:
@@ -448,8 +450,8 @@ def run_ours(args, rank, world, local_rank):
         def run_pipelined(nsteps):
             inflight = []
             for st_i in range(nsteps):
-                bufs = hout2[st_i % 2]
-                while inflight and inflight[0][0] <= st_i - 2:
+                bufs = hout2[st_i % depth]
+                while inflight and inflight[0][0] <= st_i - depth:
                     wait(inflight.pop(0)[1])
                 for nm in names:
                     jid, _, _ = ctx.submit(hpts[nm], hosts[nm][1], *bufs[nm])
@@ -474,7 +476,7 @@ def run_ours(args, rank, world, local_rank):
         d2h = sum(len(hosts[nm][0]) * hosts[nm][1] * 12 for nm in names)
         e2e = {"value": world * nq_step / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e2e_steps,
-               "api": "knnjoin_submit/knnjoin_poll, pinned host points and outputs, two steps in flight",
+               "api": f"knnjoin_submit/knnjoin_poll, pinned host points and outputs, {depth} steps in flight",
                "sequential_self_join_ms_per_step": round(seq_ms, 3)}
 
     cpu = None
@@ -762,6 +764,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--policy", type=int, choices=[0, 1], default=0,
                     help="1: the paper's GPU-Only policy (global eps, re-index eps += eps_min/2)")
+    ap.add_argument("--e2e-depth", type=int, default=2,
+                    help="steps in flight in the end-to-end measurement (each holds its own pinned outputs)")
     ap.add_argument("--tune-cache", default="",
                     help="tune cache file (JSON): joins already in it are not re-tuned")
     ap.add_argument("--no-autotune", action="store_true",
