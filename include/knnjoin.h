@@ -104,7 +104,8 @@ typedef struct {
     int d, K;
     int passes;                    /* passes of the re-queue loop */
     int start_level;
-    int64_t pass_queries[16];      /* active queries per pass (pass 0 = n) */
+    int64_t pass_queries[16];      /* active queries per pass (pass 0: every query of the join,
+                                      or of the first output chunk) */
     int64_t candidates;            /* candidate distance evaluations, all passes */
     int64_t band_entries;          /* exact re-scores (FP64-canonical) */
     int64_t overflow_queries;      /* queries redone with exact keys */
