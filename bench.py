@@ -417,6 +417,14 @@ def run_ours(args, rank, world, local_rank):
                 "scan_ms_per_step": scan_ms_per_step,
                 "join_frac": roof_ms / ms_per_step,
                 "fp32_only_frac": (alg_flops / 69.2e12 * 1e3) / ms_per_step,
+                "fp32_view": {"bound": "alu", "achieved": alg_flops / (scan_ms_per_step / 1e3) / 1e12
+                              if scan_ms_per_step > 0 else None, "peak": 69.2, "unit": "TFLOP/s",
+                              "frac": (alg_flops / (scan_ms_per_step / 1e3) / 1e12) / 69.2
+                              if scan_ms_per_step > 0 else None,
+                              "what": "W_ref*(3d-1) FP32 flops of the step / the scan launches' event time, "
+                                      "against the measured FFMA peak (profiles/alu_peaks_b300.md); the "
+                                      "kernel is issue-bound (ncu: 57-62% issue active, DRAM 1.5-4% of peak, "
+                                      "profiles/k_scan2_unif_2m.md)"},
                 "note": "frac = scan-kernel achieved / measured HBM copy peak; algorithmic bytes "
                         "credit no on-chip reuse (W_ref*4d), so frac > 1 where a candidate row "
                         "serves several queries of an item; traffic = ncu DRAM bytes of the "
