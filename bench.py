@@ -482,10 +482,34 @@ def run_ours(args, rank, world, local_rank):
         seq_ms = (time.perf_counter() - t0) * 1e3
         h2d = sum(hosts[nm][0].nbytes for nm in names)
         d2h = sum(len(hosts[nm][0]) * hosts[nm][1] * 12 for nm in names)
+
+        # the step's copies alone (pinned host <-> device, events on one stream)
+        def copy_ms(fn):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(e)
+
+        def h2d_copy():
+            for nm in names:
+                dpts[nm].copy_(hpts[nm], non_blocking=True)
+
+        def d2h_copy():
+            for nm in names:
+                hout[nm][0].copy_(outs[nm][0], non_blocking=True)
+                hout[nm][1].copy_(outs[nm][1], non_blocking=True)
+
+        h2d_ms, d2h_ms = copy_ms(h2d_copy), copy_ms(d2h_copy)
         e2e = {"value": world * nq_step / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e2e_steps,
                "api": f"knnjoin_submit/knnjoin_poll, pinned host points and outputs, {depth} steps in flight",
-               "sequential_self_join_ms_per_step": round(seq_ms, 3)}
+               "sequential_self_join_ms_per_step": round(seq_ms, 3),
+               "h2d_ms_per_step": round(h2d_ms, 3), "d2h_ms_per_step": round(d2h_ms, 3),
+               "copies": "the step's inputs and results copied alone (pinned host memory, CUDA events)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
