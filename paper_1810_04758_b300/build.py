@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libknnjoin.so")
+LIB_CHECKS = os.path.join(BUILD, "libknnjoin_checks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -34,18 +35,36 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
+def up_to_date_lib(lib: str) -> bool:
+    if not os.path.exists(lib):
+        return False
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(s) <= t for s in sources())
+
+
+def _compile(lib: str, flags: list[str], verbose: bool) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *NVCC_FLAGS, *(extra or []), "-o", LIB + ".tmp",
-           os.path.join(CSRC, "knnjoin.cu")]
+    cmd = [nvcc, *NVCC_FLAGS, *flags, "-o", lib + ".tmp", os.path.join(CSRC, "knnjoin.cu")]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    if not force and up_to_date():
+        return LIB
+    return _compile(LIB, list(extra or []), verbose)
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The checked variant (-DKNN_CHECKS): kernels test their array indexes and
+    report a failed test as KNN_ERR_CUDA instead of accessing out of bounds."""
+    if not force and up_to_date_lib(LIB_CHECKS):
+        return LIB_CHECKS
+    return _compile(LIB_CHECKS, ["-DKNN_CHECKS"], verbose)
 
 
 if __name__ == "__main__":

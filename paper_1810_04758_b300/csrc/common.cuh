@@ -8,6 +8,22 @@
 namespace knn {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// Checked build (-DKNN_CHECKS, build.py build_checked): guarded accesses test
+// their index first; a failed test sets bit `site` of g_check_word and the
+// access is skipped.  The host reads and clears the word after every join.
+// In the normal build a guard is the constant true and compiles away.
+#ifdef KNN_CHECKS
+__device__ unsigned int g_check_word;
+__device__ __forceinline__ bool knn_guard(bool ok, int site)
+{
+    if (!ok) atomicOr(&g_check_word, 1u << site);
+    return ok;
+}
+#define KNN_GUARD(cond, site) (::knn::knn_guard((cond), (site)))
+#else
+#define KNN_GUARD(cond, site) (true)
+#endif
 constexpr int MAX_DIM = 8;
 constexpr int MAX_LEVELS = 26;  // grid levels 0 .. 25 (at most 24 key bits per dimension)
 

@@ -785,7 +785,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.qperm = qperm;
                 a.self = self ? 1 : 0;
                 a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
-            a.row0 = row0;
+                a.row0 = row0;
+                a.out_rows = chunked ? chunk_rows : nq;
+                a.nq = nq;
                 a.counter = small + 3;
                 for (int L = 0; L < MAX_LEVELS; ++L) {
                     a.hslotL[L] = tabs[L].slot;
@@ -813,6 +815,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 uint32_t nitems = 0;
                 a.items = make_items(active, m, fast ? QM : SCAN_WARPS, nitems);
                 a.active = active;
+                a.nactive = m;
                 a.nitems = nitems;
                 CK(cudaMemsetAsync(small + 3, 0, 4, s));
                 CK(cudaEventRecord(evs[0], s));
@@ -838,6 +841,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                     if (mo > 0) {
                         a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
                         a.active = ovl;
+                        a.nactive = mo;
                         a.nitems = nitems;
                         CK(cudaMemsetAsync(small + 3, 0, 4, s));
                         dispatch_scan(*this, d, a, smem1);
@@ -888,6 +892,18 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     fetch(pinned, st, 4 * sizeof(unsigned long long));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+#ifdef KNN_CHECKS
+    {
+        unsigned w = 0, z = 0;
+        CK(cudaMemcpyFromSymbol(&w, g_check_word, sizeof(w)));
+        if (w) {
+            CK(cudaMemcpyToSymbol(g_check_word, &z, sizeof(z)));
+            char msg[96];
+            snprintf(msg, sizeof(msg), "bounds check failed (sites 0x%x)", w);
+            fail(KNN_ERR_CUDA, msg);
+        }
+    }
+#endif
     unsigned long long hs[4];
     memcpy(hs, pinned, sizeof(hs));
     stats.candidates = (int64_t)hs[0];

@@ -65,6 +65,9 @@ struct ScanArgs {
     int self;                  // 1: self-join (a query's own point is not its neighbour)
     float rcap;                // > 0: certificate radius capped at this (the paper's policy)
     int64_t row0;              // first output row held by out_ids/out_dist (chunked output)
+    int64_t out_rows;          // output rows held (bounds of the checked build)
+    int64_t nq;                // queries (sorted query positions < nq)
+    int64_t nactive;           // entries of `active`
     int CH;                    // staged candidates per chunk
     int noff;                  // 3^d
 };
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                         const int t = base + lane;
                         bool valid = t < clen;
                         uint32_t s = valid ? cs[t] : 0u;
-                        valid = valid && s != qself;
+                        valid = valid && s != qself && KNN_GUARD(s < a.n, 8);
                         if (!exact_round) {
                             float d2 = 0.0f;
                             if (valid) {
@@ -460,9 +463,11 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 }
             }
             if (certified) {
-                const int64_t row = ((int64_t)a.qperm[qs] - a.row0) * K;
+                const int64_t rowq = (int64_t)a.qperm[qs] - a.row0;
+                const bool rowok = KNN_GUARD(rowq >= 0 && rowq < a.out_rows, 9);
+                const int64_t row = rowq * K;
                 for (int u = 0; u < mine; ++u)
-                    if (rr[u] < (uint32_t)K) {
+                    if (rr[u] < (uint32_t)K && rowok) {
                         a.out_ids[row + rr[u]] = (int32_t)rid[u];
                         a.out_dist[row + rr[u]] = __longlong_as_double((long long)rd[u]);  // D; k_sqrt_rows converts
                     }

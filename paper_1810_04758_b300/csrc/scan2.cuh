@@ -441,7 +441,8 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
         if (lane == 0) qc[i * QP + DIM] = tnew;
         __syncwarp();
     }
-    if (acc) bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
+    if (acc && KNN_GUARD(c0 + __popc(bal & lanemask_lt()) < B, 4))
+        bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
     if (lane == i) my_cnt = c0 < 0 ? -1 : c0 + nnew;
 }
 
@@ -457,7 +458,8 @@ __device__ __forceinline__ uint32_t super_tile_mask(const ScanArgs &a, uint32_t 
                                                     int Q, int lane)
 {
     constexpr int QP = query_row_floats(DIM);
-    const uint64_t k0 = a.keys[sb], k1 = a.keys[se - 1];
+    const uint64_t k0 = KNN_GUARD(se <= (uint64_t)a.n && sb < se, 3) ? a.keys[sb] : 0,
+                   k1 = KNN_GUARD(se <= (uint64_t)a.n && sb < se, 3) ? a.keys[se - 1] : ~0ull;
     const uint64_t x = k0 ^ k1;
     const int hb = x ? 64 - __clzll((long long)x) : 0;  // free low key bits
     float blo = 0.0f, bhi = 0.0f;
@@ -603,8 +605,9 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
         const uint4 *hslot = a.hslotL[level];
         const uint32_t hmask = a.hmaskL[level];
 
-        if (lane < Q) {
+        if (lane < Q && KNN_GUARD(it.x + lane < (uint64_t)a.nactive, 0)) {
             uint32_t s = a.active[it.x + lane];
+            if (!KNN_GUARD(s < (uint64_t)a.nq, 1)) s = 0;
             float c[DIM];
             load_point<DIM>(a.qxsort, s, c);
             qsv[lane] = s;
@@ -789,8 +792,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     float cA[DIM], cB[DIM];
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
-                    if (vA) load_point<DIM>(a.xsort, sA, cA);
-                    if (vB) load_point<DIM>(a.xsort, sB, cB);
+                    if (vA && KNN_GUARD(sA < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sA, cA);
+                    if (vB && KNN_GUARD(sB < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sB, cB);
                     st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
                     KNN_ITEM_TILE(__popc(tmask) * 2);
                     scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane);
@@ -873,7 +876,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     if (g < m) {
                         const uint32_t s = (uint32_t)bi[v[e] & SLOT];
                         float c[DIM];
-                        load_point<DIM>(a.xsort, s, c);
+                        if (KNN_GUARD(s < (uint64_t)a.n, 7)) load_point<DIM>(a.xsort, s, c);
+                        else for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
                         uint64_t bits = 0;
                         bool done = false;
                         if (a.fixed_ok) {
@@ -915,11 +919,13 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
                 if (certified) {
                     flag = 0;
-                    const int64_t row = ((int64_t)a.qperm[qsv[i]] - a.row0) * K;
+                    const int64_t rowq = (int64_t)a.qperm[qsv[i]] - a.row0;
+                    const bool rowok = KNN_GUARD(rowq >= 0 && rowq < a.out_rows, 5);
+                    const int64_t row = rowq * K;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int g = lane * E + e;
-                        if (g < K) {
+                        if (g < K && rowok) {
                             a.out_ids[row + g] = (int32_t)I[e];
                             a.out_dist[row + g] = __longlong_as_double((long long)D[e]);  // D; k_sqrt_rows converts
                         }
