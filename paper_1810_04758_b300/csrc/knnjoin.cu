@@ -15,6 +15,7 @@
 // Around it: the context, the worker pool for batched and served joins, the
 // autotuner's table, and the allocation-free entry point.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -142,6 +143,15 @@ bool is_device_ptr(const void *p)
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+// Named NVTX range for the lifetime of the object (tracing with nsys/ncu;
+// no-ops without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Autotuned cell-width multipliers, keyed by (d, K, floor(log2 n)), shared by
@@ -466,6 +476,7 @@ void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
 void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
                    const float *qry_in, int64_t nq_in)
 {
+    NvtxRange trace_join(qry_in ? "knnjoin: R x S join" : "knnjoin: self-join");
     const bool self = qry_in == nullptr;
     const int64_t nq = self ? n : nq_in;  // queries (output rows)
     CK(cudaSetDevice(device));
@@ -520,6 +531,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     CK(cudaEventRecord(ev[0], s));
 
     // a1
+    std::unique_ptr<NvtxRange> trace_phase(new NvtxRange("a1-a2 bounding box, search distance"));
     PrepReduce *red = sc.get<PrepReduce>("red", 1);
     GridParams *gp = sc.get<GridParams>("gp", 1);
     unsigned long long *st = sc.get<unsigned long long>("stats", 8);
@@ -592,6 +604,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     float eps_mult = 1.0f;
     for (int epoch = 0;; ++epoch) {
         // a3-a5
+        trace_phase.reset(new NvtxRange("a3-a6 keys, sort, gather, start levels"));
         uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
         uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
         k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
@@ -758,6 +771,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             }
             row0 = r0;
             while (m > 0) {
+                char pass_name[32];
+                snprintf(pass_name, sizeof(pass_name), "pass %d", pass);
+                trace_phase.reset(new NvtxRange(pass_name));
                 if (pass > (policy == 1 ? 8192 : 4 * MAX_LEVELS)) fail(KNN_ERR_CUDA, "internal: too many passes");
                 // order the active list by level (stable: positions stay ordered
                 // within a level) and build the levels' hash maps
@@ -877,6 +893,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
         hp = read1(gp);
     }
+    trace_phase.reset(new NvtxRange("a11 square roots, result copy"));
     stats.start_level = first_level;
     stats.passes = pass;
     if (!chunked) {
