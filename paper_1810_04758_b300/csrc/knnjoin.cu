@@ -838,19 +838,19 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 if (fast) dispatch_scan2(*this, d, E2, a, smem2);
                 else dispatch_scan(*this, d, a, smem1);
                 CK(cudaEventRecord(evs[1], s));
-                {
-                    CK(cudaEventSynchronize(evs[1]));
+                // the scan's time and candidate count, read after the pass's
+                // last readback has synchronised the stream (no wait here)
+                fetch(pinned + 8, st, sizeof(unsigned long long));
+                auto read_pass = [&] {
                     float t = 0.f;
                     CK(cudaEventElapsedTime(&t, evs[0], evs[1]));
                     ms_scan += t;
                     if (pass < 16) stats.ms_pass[pass] = t;
-                    fetch(pinned + 8, st, sizeof(unsigned long long));
-                    CK(cudaStreamSynchronize(s));
                     unsigned long long c;
                     memcpy(&c, pinned + 8, sizeof(c));
                     if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
                     cand_before = (int64_t)c;
-                }
+                };
                 if (fast) {
                     // queries whose buffer overflowed (massive ties): general kernel
                     int64_t mo = select_list(active, m, 2, ovl);
@@ -867,6 +867,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 if (policy == 1) {
                     k_mark_done<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, qperm, done); ++launches;
                     int64_t left = select_list(active, m, 1, active2);
+                    read_pass();
                     if (pass < 16) stats.pass_queries[pass] = m;
                     ++pass;
                     m = left;
@@ -874,6 +875,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 }
                 k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
                 int64_t next = select_list(active, m, 1, active2);
+                read_pass();
                 if (pass < 16) stats.pass_queries[pass] = m;
                 std::swap(active, active2);
                 m = next;
