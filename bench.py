@@ -511,6 +511,18 @@ def run_ours(args, rank, world, local_rank):
                "h2d_ms_per_step": round(h2d_ms, 3), "d2h_ms_per_step": round(d2h_ms, 3),
                "copies": "the step's inputs and results copied alone (pinned host memory, CUDA events)"}
 
+    # FP32-only id mismatch (untimed): how often ranking by the FP32 filter
+    # distance alone would change the exact rows, on strided sampled rows
+    fp32_only = None
+    if rank == 0 and args.fp32_rows > 0:
+        fp32_only = {}
+        for nm in names:
+            n_ = len(hosts[nm][0])
+            m = min(args.fp32_rows, n_)
+            res = ctx.fp32_mismatch(dpts[nm], outs[nm][0], range(0, n_, n_ // m)[:m])
+            fp32_only[nm] = {k: res[k] for k in ("rows", "positions_differing", "ids_missing",
+                                                  "id_mismatch_rate", "row_mismatch_rate")}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
@@ -538,6 +550,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "fp32_only_mismatch": fp32_only,
         "policy": "paper GPU-Only (global eps, re-index)" if args.policy == 1 else "certified rings",
         "sequential_ms_per_step": seq_ms_per_step,
         "step_api": "knnjoin_self_join_batch (the three joins on the worker pool); per-join stats, "
@@ -794,6 +807,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--fp32-rows", type=int, default=65536,
+                    help="sampled rows per point set for the FP32-only mismatch rate (0: skip)")
     ap.add_argument("--policy", type=int, choices=[0, 1], default=0,
                     help="1: the paper's GPU-Only policy (global eps, re-index eps += eps_min/2)")
     ap.add_argument("--e2e-depth", type=int, default=2,

@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct knnjoin_ctx knnjoin_ctx;
+typedef struct knnjoin_index knnjoin_index;  /* resident index (knnjoin_index_create) */
 
 typedef enum {
     KNN_OK = 0,
@@ -159,6 +160,38 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
 knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, const float *points, int64_t n,
                             int d, int K, int32_t *out_ids, double *out_dist);
 
+/* Resident index: index a data set once and keep it on the device, then
+ * answer R x S queries against it (the same result as knnjoin_join with these
+ * points: for each query row the K nearest data rows under (D, j), nothing
+ * excluded).  The paper indexes a data set once on the GPU and sends it query
+ * batches (Sec. 3.1 index, Sec. 4.3 batches); serving keeps the index of a
+ * data set between requests instead of rebuilding it per join.
+ *
+ * knnjoin_index_create: points row-major float32 [n][d], host or device,
+ *   read during the call only (the index keeps its own copy, sorted); K is
+ *   the neighbour count the search distance is chosen for (queries may ask
+ *   for another).  Size rules as knnjoin_self_join.  *out receives the index,
+ *   owned by the library until knnjoin_index_destroy or knnjoin_destroy of
+ *   the context.  The index holds about (24 + 4 d + 4 pad(d)) n bytes of
+ *   device memory plus its cell maps (pad(d) = 2, 4 or 8).
+ * knnjoin_index_query: queries row-major float32 [nq][d], host or device;
+ *   out_ids int32 [nq][K], out_dist float64 [nq][K], host or device;
+ *   1 <= K <= min(n, 256).  The grid is the data's: queries outside its box
+ *   are answered exactly (boundary cells, wider rings), only more slowly.
+ *   Calls on one index are serialised; different indexes run concurrently
+ *   (each has its own stream).  Work queued on the context's stream before
+ *   the call completes first.  KNN_ERR_INVALID for nq < 1, K out of range,
+ *   NULL pointers or a NaN/Inf query coordinate.
+ * knnjoin_index_stats: counters of the index's last call (create or query).
+ * knnjoin_index_destroy: frees the index; NULL or an already destroyed index
+ *   is ignored. */
+knnjoin_status knnjoin_index_create(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                    knnjoin_index **out);
+knnjoin_status knnjoin_index_query(knnjoin_index *index, const float *queries, int64_t nq, int K,
+                                   int32_t *out_ids, double *out_dist);
+knnjoin_status knnjoin_index_stats(knnjoin_index *index, knnjoin_stats *out);
+void knnjoin_index_destroy(knnjoin_index *index);
+
 /* Autotuning (not in the paper; its analogue is the search-distance factor
  * study of Sec. 5.4): time the self-join of these points at a fixed list of
  * cell-width multipliers (1.0 .. 1.625, best of two runs each, outputs in
@@ -194,6 +227,28 @@ knnjoin_status knnjoin_cancel(knnjoin_ctx *ctx, uint64_t job_id);
 
 /* Counters of a job (job_id 0: the last blocking join). */
 knnjoin_status knnjoin_get_stats(knnjoin_ctx *ctx, uint64_t job_id, knnjoin_stats *out);
+
+/* Diagnostic, not part of a join: how often ranking by the FP32 filter
+ * distance alone would have changed a self-join's result.  The join filters
+ * with an FP32 squared distance and ranks in canonical FP64 (Sec. 4, the
+ * kernel; Sec. 2.1 defines the result); this call takes exact result rows
+ * (out_ids of knnjoin_self_join for these points and K) and, for each listed
+ * query row i, forms the FP32-only row: the K smallest j != i under
+ * (d2_32(i, j), j), d2_32 being the scan kernels' own FP32 expression, by a
+ * brute-force scan of all n points on the device.
+ *   points      row-major float32 [n][d], host or device;
+ *   ids         int32 [n][K] exact rows, host or device;
+ *   rows        int64 [nrows] query rows to check, HOST memory, each in [0, n);
+ *   out_counts  int64 [3], host: [0] rows whose FP32-only row differs at any
+ *               position, [1] positions that differ, summed over the rows,
+ *               [2] exact ids absent from the FP32-only row, summed.
+ * Cost: nrows * n FP32 distance evaluations.  KNN_ERR_INVALID for the
+ * self-join's size rules, nrows < 1, a row outside [0, n), device-memory
+ * rows, NULL pointers, or an ids row holding an index outside [0, n) or the
+ * row itself. */
+knnjoin_status knnjoin_fp32_mismatch(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                     const int32_t *ids, const int64_t *rows, int64_t nrows,
+                                     int64_t *out_counts);
 
 /* Message of the last error on this context ("" if none).  Valid until the
  * next call on the context. */

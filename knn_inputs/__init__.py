@@ -120,6 +120,22 @@ def points_duplicates(copies: int, sites: int, d: int, key: int) -> np.ndarray:
     return pts[perm]
 
 
+def points_columns(columns: int, per_column: int, key: int, jitter_bits: int = 16,
+                   jitter_scale: float = 2.0 ** -29) -> np.ndarray:
+    """Two-dimensional points on `columns` integer x positions with
+    `per_column` points each; y = k * jitter_scale, k uniform in
+    [0, 2^jitter_bits).  Distances across columns differ only in terms far
+    below single precision, so FP32 squared distances tie where the exact
+    ones do not.  Shuffled order, float32."""
+    m = columns * per_column
+    x = np.repeat(np.arange(columns, dtype=np.float64), per_column)
+    k = raw_u64(key, m) >> np.uint64(64 - jitter_bits)
+    y = k.astype(np.float64) * jitter_scale
+    pts = np.stack([x, y], axis=1)
+    perm = np.argsort(raw_u64(key, m, offset=m), kind="stable")
+    return pts[perm].astype(np.float32)
+
+
 def permutation(n: int, key: int) -> np.ndarray:
     """A seeded permutation of range(n)."""
     return np.argsort(raw_u64(key, n), kind="stable")

@@ -31,6 +31,8 @@ _libs: dict[str, ctypes.CDLL] = {}
 
 MUTANTS = ("DROP_LAST_TERM", "TIE_DESC", "KEEP_SELF", "LOOSE_CERTIFICATE",
            "NO_LOWER_NEIGHBOUR")
+# planted mistakes in the FP32-only ranking (caught by its own pins)
+FP32_MUTANTS = ("FP32_ONE_CHAIN", "FP32_UNFUSED")
 
 
 def _lib_path(mutant: str | None) -> str:
@@ -48,7 +50,7 @@ def build(mutant: str | None = None, force: bool = False) -> str:
            "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard",
            "-o", out + ".tmp", _SRC, "-lm"]
     if mutant:
-        if mutant not in MUTANTS:
+        if mutant not in MUTANTS + FP32_MUTANTS:
             raise ValueError(mutant)
         cmd.insert(1, f"-DORACLE_MUTANT_{mutant}")
     subprocess.run(cmd, check=True)
@@ -77,6 +79,9 @@ def _load(mutant: str | None = None) -> ctypes.CDLL:
             lib.oracle_bf_rs.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                          P, P, ctypes.c_int]
             lib.oracle_bf_rs.restype = ctypes.c_int
+            lib.oracle_fp32_rows.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P,
+                                             ctypes.c_int64, P, ctypes.c_int]
+            lib.oracle_fp32_rows.restype = ctypes.c_int
             lib.oracle_grid.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, P, P, P, ctypes.c_int]
             lib.oracle_grid.restype = ctypes.c_int
@@ -144,6 +149,31 @@ def bf_rows(points: np.ndarray, K: int, rows, threads: int = 0, mutant: str | No
     if rc:
         raise ValueError("oracle_bf_rows: invalid arguments")
     return ids, dist
+
+
+def fp32_rows(points: np.ndarray, K: int, rows, threads: int = 0, mutant: str | None = None):
+    """For the query rows `rows`, the K nearest under the FP32 filter distance
+    alone, ties by index, self excluded: ids int32 [len(rows), K]."""
+    p = _prep(points)
+    n, d = p.shape
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    ids = np.empty((len(r), K), np.int32)
+    rc = _load(mutant).oracle_fp32_rows(_ptr(p), n, d, K, _ptr(r), len(r), _ptr(ids), threads)
+    if rc:
+        raise ValueError("oracle_fp32_rows: invalid arguments")
+    return ids
+
+
+def fp32_mismatch(points: np.ndarray, exact_ids: np.ndarray, rows, threads: int = 0):
+    """Counts of how the FP32-only rows differ from the exact rows
+    `exact_ids[rows]`: (rows differing anywhere, positions differing, exact
+    ids absent from the FP32-only row)."""
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    want = np.asarray(exact_ids)[r]
+    got = fp32_rows(points, want.shape[1], r, threads)
+    diff = got != want
+    missing = sum(len(np.setdiff1d(want[k], got[k])) for k in range(len(r)))
+    return int(diff.any(axis=1).sum()), int(diff.sum()), int(missing)
 
 
 def grid(points: np.ndarray, K: int, width_mult: float = 1.0, threads: int = 0,

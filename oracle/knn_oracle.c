@@ -26,6 +26,9 @@
  *                   a set R, the K nearest points of a data set S under the
  *                   same order, nothing excluded (the self-join applied to a
  *                   query set apart from the data, as Sec. 2.1 notes).
+ *   oracle_fp32_rows  for chosen query rows, the K nearest under the FP32
+ *                   filter distance alone (see below): what ranking without
+ *                   the FP64 re-score would return.
  *   oracle_grid     an exact grid join in the paper's manner (Sec. 3.1 grid of
  *                   non-empty cells, Sec. 4.4 epsilon selection, ring of 3^n
  *                   adjacent cells, failed queries retried with a wider
@@ -167,6 +170,77 @@ int oracle_bf_rs(const float *qry, int64_t nq, const float *pts, int64_t n, int 
             for (int64_t j = 0; j < n; ++j)
                 topk_insert(top, &cnt, K, canon_d2(q, pts + j * d, d), (int32_t)j);
             write_row(top, K, ids + r * K, dist + r * K);
+        }
+        free(top);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP32-only ranking (diagnostic).                                     */
+/*                                                                      */
+/* The GPU join filters candidates with a single-precision squared      */
+/* distance and ranks the survivors in canonical FP64.  The filter's    */
+/* value, written here independently: every difference                 */
+/* t_k = fl32(x_ik - x_jk); for d < 4 one accumulator                   */
+/* s = fma32(t_k, t_k, s) over k = 0..d-1 (one rounding per fused       */
+/* step); for d >= 4 two accumulators, even k into e and odd k into o,  */
+/* each fma32(t_k, t_k, .), then fl32(e + o).  oracle_fp32_rows ranks   */
+/* all j != i by (that value, j) and keeps the K smallest.  Parity      */
+/* unpinned against the paper (which fixes no precision); pinned in the */
+/* tests by an exact-rational emulation of single-precision rounding.   */
+/* ------------------------------------------------------------------ */
+static float filter_d2_32(const float *a, const float *b, int d)
+{
+#ifdef ORACLE_MUTANT_FP32_ONE_CHAIN
+    if (d < 9) {
+#else
+    if (d < 4) {
+#endif
+        float s = 0.0f;
+        for (int k = 0; k < d; ++k) {
+            float t = a[k] - b[k];
+#ifdef ORACLE_MUTANT_FP32_UNFUSED
+            float sq = t * t;
+            s = s + sq;
+#else
+            s = fmaf(t, t, s);
+#endif
+        }
+        return s;
+    }
+    float e = 0.0f, o = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        float t = a[k] - b[k];
+        if (k & 1)
+            o = fmaf(t, t, o);
+        else
+            e = fmaf(t, t, e);
+    }
+    return e + o;
+}
+
+int oracle_fp32_rows(const float *pts, int64_t n, int d, int K,
+                     const int64_t *rows, int64_t nrows, int32_t *ids, int nthreads)
+{
+    if (!pts || !rows || !ids || n < 2 || d < 1 || K < 1 || K > n - 1)
+        return -1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= n) return -1;
+    int nt = threads_or_default(nthreads);
+    #pragma omp parallel num_threads(nt)
+    {
+        nb_t *top = (nb_t *)malloc(sizeof(nb_t) * (size_t)K);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int cnt = 0;
+            const int64_t i = rows[r];
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                /* a float widened to double keeps its value and order */
+                topk_insert(top, &cnt, K, (double)filter_d2_32(pts + i * d, pts + j * d, d), (int32_t)j);
+            }
+            for (int k = 0; k < K; ++k) ids[r * K + k] = top[k].id;
         }
         free(top);
     }

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional
+from typing import Optional, Sequence
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libknnjoin.so")
@@ -32,7 +32,9 @@ STATUS_NAMES = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_NOMEM", 3: "KNN_E
 EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_join", "knnjoin_autotune",
            "knnjoin_self_join_batch",
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
-           "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc")
+           "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc",
+           "knnjoin_fp32_mismatch", "knnjoin_index_create", "knnjoin_index_query",
+           "knnjoin_index_stats", "knnjoin_index_destroy")
 KNN_NOALLOC_MAX_POINTS = 65536
 
 
@@ -108,6 +110,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_join.restype = I
     lib.knnjoin_autotune.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_float)]
     lib.knnjoin_autotune.restype = I
+    lib.knnjoin_fp32_mismatch.argtypes = [P, P, I64, I, I, P, ctypes.POINTER(ctypes.c_int64), I64,
+                                          ctypes.POINTER(ctypes.c_int64)]
+    lib.knnjoin_fp32_mismatch.restype = I
+    lib.knnjoin_index_create.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_void_p)]
+    lib.knnjoin_index_create.restype = I
+    lib.knnjoin_index_query.argtypes = [P, P, I64, I, P, P]
+    lib.knnjoin_index_query.restype = I
+    lib.knnjoin_index_stats.argtypes = [P, ctypes.POINTER(KnnjoinStats)]
+    lib.knnjoin_index_stats.restype = I
+    lib.knnjoin_index_destroy.argtypes = [P]
+    lib.knnjoin_index_destroy.restype = None
     lib.knnjoin_self_join_batch.argtypes = [P, ctypes.POINTER(KnnjoinJob), I]
     lib.knnjoin_self_join_batch.restype = I
     lib.knnjoin_submit.argtypes = [P, ctypes.POINTER(KnnjoinJob), ctypes.POINTER(ctypes.c_uint64)]
@@ -172,6 +185,37 @@ def knnjoin_autotune(ctx: int, points: int, n: int, d: int, K: int) -> float:
     best = ctypes.c_float(0.0)
     _check(ctx, load_library().knnjoin_autotune(ctx, points, n, d, K, ctypes.byref(best)))
     return float(best.value)
+
+
+def knnjoin_fp32_mismatch(ctx: int, points: int, n: int, d: int, K: int, ids: int,
+                          rows: Sequence[int]) -> tuple[int, int, int]:
+    arr = (ctypes.c_int64 * len(rows))(*rows)
+    out = (ctypes.c_int64 * 3)()
+    _check(ctx, load_library().knnjoin_fp32_mismatch(ctx, points, n, d, K, ids, arr, len(rows), out))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def knnjoin_index_create(ctx: int, points: int, n: int, d: int, K: int) -> int:
+    out = ctypes.c_void_p(0)
+    _check(ctx, load_library().knnjoin_index_create(ctx, points, n, d, K, ctypes.byref(out)))
+    return int(out.value)
+
+
+def knnjoin_index_query(ctx: int, index: int, queries: int, nq: int, K: int, out_ids: int,
+                        out_dist: int) -> int:
+    # errors are reported through the index's context
+    return _check(ctx, load_library().knnjoin_index_query(index, queries, nq, K, out_ids, out_dist))
+
+
+def knnjoin_index_stats(index: int) -> dict:
+    st = KnnjoinStats()
+    if load_library().knnjoin_index_stats(index, ctypes.byref(st)) != KNN_OK:
+        raise KnnJoinError(KNN_ERR_INVALID, "invalid index")
+    return st.as_dict()
+
+
+def knnjoin_index_destroy(index: int) -> None:
+    load_library().knnjoin_index_destroy(index)
 
 
 def knnjoin_self_join_batch(ctx: int, jobs: list[KnnjoinJob]) -> int:
@@ -294,6 +338,35 @@ class Context:
         n, d = points.shape
         return knnjoin_autotune(self.ctx, points.data_ptr(), n, d, K)
 
+    def fp32_mismatch(self, points, ids, rows) -> dict:
+        """For the listed query rows of a self-join result `ids` (int32 [n, K])
+        of `points` (float32 [n, d]), compare with ranking by the FP32 filter
+        distance alone; returns the counts and rates of rows, positions and
+        ids that would differ."""
+        torch = self._torch
+        if points.dtype != torch.float32 or points.dim() != 2:
+            raise ValueError("points must be a float32 [n, d] tensor")
+        if ids.dtype != torch.int32 or ids.dim() != 2 or ids.shape[0] != points.shape[0]:
+            raise ValueError("ids must be an int32 [n, K] tensor")
+        points, ids = points.contiguous(), ids.contiguous()
+        n, d = points.shape
+        K = ids.shape[1]
+        rows = [int(r) for r in rows]
+        rw, pw, miss = knnjoin_fp32_mismatch(self.ctx, points.data_ptr(), n, d, K, ids.data_ptr(), rows)
+        m = len(rows)
+        return {"rows": m, "K": K, "rows_differing": rw, "positions_differing": pw, "ids_missing": miss,
+                "row_mismatch_rate": rw / m, "id_mismatch_rate": pw / (m * K), "set_mismatch_rate": miss / (m * K)}
+
+    def index(self, points, K: int) -> "Index":
+        """Index the float32 [n, d] `points` (host or device) once and keep the
+        index on the device; its `query` answers R x S joins against them."""
+        torch = self._torch
+        if points.dtype != torch.float32 or points.dim() != 2:
+            raise ValueError("points must be a float32 [n, d] tensor")
+        points = points.contiguous()
+        n, d = points.shape
+        return Index(self, knnjoin_index_create(self.ctx, points.data_ptr(), n, d, K), n, d)
+
     def join(self, queries, points, K: int, out_ids=None, out_dist=None):
         """R x S join: for each row of the float32 [nq, d] `queries`, the K
         nearest rows of the float32 [n, d] `points` (nothing excluded).
@@ -349,3 +422,45 @@ class Context:
 
     def last_error(self) -> str:
         return knnjoin_last_error(self.ctx)
+
+
+class Index:
+    """A resident index of one point set (knnjoin_index_*): built once, then
+    queried with batches of query points; freed by close() or with its
+    context."""
+
+    def __init__(self, ctx: Context, handle: int, n: int, d: int):
+        self._ctx = ctx
+        self.handle = handle
+        self.n = n
+        self.d = d
+
+    def query(self, queries, K: int, out_ids=None, out_dist=None):
+        """For each row of the float32 [nq, d] `queries`, the K nearest indexed
+        points (nothing excluded): (ids int32 [nq, K], dist float64 [nq, K]) on
+        the queries' device."""
+        torch = self._ctx._torch
+        if not self.handle:
+            raise ValueError("index is closed")
+        if queries.dtype != torch.float32 or queries.dim() != 2 or queries.shape[1] != self.d:
+            raise ValueError("queries must be a float32 [nq, d] tensor with the index's d")
+        queries = queries.contiguous()
+        nq = queries.shape[0]
+        out_ids, out_dist = self._ctx._outputs(nq, K, queries, out_ids, out_dist)
+        knnjoin_index_query(self._ctx.ctx, self.handle, queries.data_ptr(), nq, K, out_ids.data_ptr(),
+                            out_dist.data_ptr())
+        return out_ids, out_dist
+
+    def stats(self) -> dict:
+        return knnjoin_index_stats(self.handle)
+
+    def close(self) -> None:
+        if self.handle and getattr(self._ctx, "ctx", None):
+            knnjoin_index_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -29,6 +29,7 @@
 #include <tuple>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -41,6 +42,7 @@
 #include "primitives.cuh"
 #include "scan.cuh"
 #include "scan2.cuh"
+#include "diag.cuh"
 
 using namespace knn;
 
@@ -224,6 +226,13 @@ struct TuneTable {
 // ---------------------------------------------------------------------------
 // One join pipeline (stream + scratch + pinned readback).
 // ---------------------------------------------------------------------------
+// Hash map from the cell keys of one grid level to their runs of points.
+struct LevelTab {
+    uint4 *slot = nullptr;
+    uint32_t mask = 0;
+    bool built = false;
+};
+
 struct Pipeline {
     int device = 0;
     int nsm = 148;
@@ -246,6 +255,17 @@ struct Pipeline {
     // SMs and one join's copy overlaps the next one's kernels
     std::mutex *big_token = nullptr;
     static constexpr int64_t BIG_JOB_ENTRIES = (int64_t)1 << 25;
+    // resident index (knnjoin_index_*): res_mode 1 makes run() index the
+    // data and keep it -- sorted keys, permutation, gathered coordinates,
+    // parameters and, as they are built, the level hash maps; res_mode 2
+    // makes run() answer R x S queries against what was kept
+    int res_mode = 0;
+    uint64_t *res_keys = nullptr;
+    uint32_t *res_perm = nullptr;
+    float *res_xsort = nullptr;
+    GridParams res_hp{};
+    float res_wm = 0.0f;
+    LevelTab res_tabs[MAX_LEVELS];
 
     void init(int dev, cudaStream_t stream, Allocator *al)
     {
@@ -479,6 +499,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     NvtxRange trace_join(qry_in ? "knnjoin: R x S join" : "knnjoin: self-join");
     const bool self = qry_in == nullptr;
     const int64_t nq = self ? n : nq_in;  // queries (output rows)
+    const int rmode = res_mode;           // 1: build a resident index, 2: query one
     CK(cudaSetDevice(device));
     const bool pts_dev = is_device_ptr(pts_in);
     const bool ids_dev = is_device_ptr(ids_in);
@@ -495,7 +516,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.K = K;
 
     const float *pts = pts_in;
-    if (!pts_dev) {
+    if (!pts_dev && rmode != 2) {  // a resident index keeps the data on the device
         float *p = sc.get<float>("pts_in", (size_t)n * d);
         CK(cudaMemcpyAsync(p, pts_in, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
         pts = p;
@@ -513,7 +534,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // exceed out_chunk_bytes) are computed in chunks of query rows, each
     // copied out before the next
     int64_t chunk_rows = nq;
-    if (policy == 0 && !(ids_dev && dist_dev)) {
+    if (policy == 0 && rmode != 1 && !(ids_dev && dist_dev)) {
         const size_t row_bytes = (size_t)K * (sizeof(int32_t) + sizeof(double));
         size_t limit = out_chunk_bytes;
         if (limit == 0) {
@@ -526,8 +547,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     }
     const bool chunked = chunk_rows < nq;
     stats.chunks = (nq + chunk_rows - 1) / chunk_rows;
-    int32_t *ids = ids_dev ? ids_in : sc.get<int32_t>("ids_out", (size_t)chunk_rows * K);
-    double *dist = dist_dev ? dist_in : sc.get<double>("dist_out", (size_t)chunk_rows * K);
+    int32_t *ids = ids_dev || rmode == 1 ? ids_in : sc.get<int32_t>("ids_out", (size_t)chunk_rows * K);
+    double *dist = dist_dev || rmode == 1 ? dist_in : sc.get<double>("dist_out", (size_t)chunk_rows * K);
     CK(cudaEventRecord(ev[0], s));
 
     // a1
@@ -536,21 +557,6 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     GridParams *gp = sc.get<GridParams>("gp", 1);
     unsigned long long *st = sc.get<unsigned long long>("stats", 8);
     CK(cudaMemsetAsync(st, 0, 8 * sizeof(unsigned long long), s));
-    k_init_reduce<<<1, 256, 0, s>>>(red); ++launches;
-    float *xs = sc.get<float>("xs", (size_t)n * d);
-    k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red); ++launches;
-    // R x S: the bounding box and fixed-point frame cover the queries too, so
-    // every query lies in the grid; the search distance and the index are
-    // the data set's
-    float *rxs = nullptr;
-    if (!self) {
-        rxs = sc.get<float>("rxs", (size_t)nq * d);
-        k_prep<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qry, nq, d, rxs, red); ++launches;
-    }
-    // a2
-    int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
-    smp = std::min(smp, n);
-    k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red); ++launches;
     const float wmul = force_wm > 0.0f ? force_wm : (tune ? tune->lookup(d, K, n) : width_mult);
     stats.width_mult = wmul;
     ParamsIn pin;
@@ -567,20 +573,57 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         pin.max_finer = 0;
         stats.width_mult = 1.0;
     }
-    float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
-    float *mrow = sc.get<float>("eps_mrow", (size_t)pin.m * 8);
-    k_eps_rows<<<grid_for(pin.S + pin.m, 256, nsm), 256, 0, s>>>(xs, n, d, pin.S, pin.m, srow, mrow); ++launches;
-    const unsigned gm = (unsigned)((pin.m + 255) / 256);
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
-    k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 0); ++launches;
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
-    k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 1); ++launches;
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
-    k_eps_count<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red); ++launches;
-    k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
-    CK(cudaGetLastError());
-    GridParams hp = read1(gp);
-    if (hp.nonfinite) fail(KNN_ERR_INVALID, "points contain a NaN or infinite coordinate");
+    float *xs = nullptr, *rxs = nullptr;
+    GridParams hp;
+    if (rmode == 2) {
+        // resident index: the data side is kept; prepare the queries only.
+        // The grid and the fixed-point frame are the data's: a query outside
+        // the data's box falls in a boundary cell (cell_of clamps), which
+        // keeps every gap and certificate a lower bound, and a batch whose
+        // coordinates leave the fixed-point frame uses the FP64 scoring path.
+        PrepReduce *qred = sc.get<PrepReduce>("qred", 1);
+        k_init_reduce<<<1, 256, 0, s>>>(qred); ++launches;
+        rxs = sc.get<float>("rxs", (size_t)nq * d);
+        k_prep<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qry, nq, d, rxs, qred); ++launches;
+        CK(cudaGetLastError());
+        fetch(pinned, &qred->min_lsb, 3 * sizeof(int));
+        CK(cudaStreamSynchronize(s));
+        int qf[3];
+        memcpy(qf, pinned, sizeof(qf));
+        if (qf[2]) fail(KNN_ERR_INVALID, "queries contain a NaN or infinite coordinate");
+        hp = res_hp;
+        stats.width_mult = res_wm;
+        if (hp.fixed_ok && qf[1] >= qf[0]) hp.fixed_ok = (qf[0] >= -hp.F && qf[1] + hp.F <= 29) ? 1 : 0;
+    } else {
+        k_init_reduce<<<1, 256, 0, s>>>(red); ++launches;
+        xs = sc.get<float>("xs", (size_t)n * d);
+        k_prep<<<grid_for(n, 256, nsm), 256, 0, s>>>(pts, n, d, xs, red); ++launches;
+        // R x S: the bounding box and fixed-point frame cover the queries too, so
+        // every query lies in the grid; the search distance and the index are
+        // the data set's
+        if (!self) {
+            rxs = sc.get<float>("rxs", (size_t)nq * d);
+            k_prep<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qry, nq, d, rxs, red); ++launches;
+        }
+        // a2
+        int64_t smp = std::min<int64_t>(2000, std::max<int64_t>(2, llround(0.001 * (double)n)));
+        smp = std::min(smp, n);
+        k_eps_pairs<<<grid_for(smp * smp, 256, nsm), 256, 0, s>>>(xs, n, d, smp, red); ++launches;
+        float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
+        float *mrow = sc.get<float>("eps_mrow", (size_t)pin.m * 8);
+        k_eps_rows<<<grid_for(pin.S + pin.m, 256, nsm), 256, 0, s>>>(xs, n, d, pin.S, pin.m, srow, mrow); ++launches;
+        const unsigned gm = (unsigned)((pin.m + 255) / 256);
+        k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
+        k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 0); ++launches;
+        k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
+        k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 1); ++launches;
+        k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
+        k_eps_count<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red); ++launches;
+        k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
+        CK(cudaGetLastError());
+        hp = read1(gp);
+        if (hp.nonfinite) fail(KNN_ERR_INVALID, "points contain a NaN or infinite coordinate");
+    }
     stats.eps_mean = hp.eps_mean;
     stats.eps_min = hp.eps_min;
     stats.cell_width = hp.w0;
@@ -605,12 +648,38 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     for (int epoch = 0;; ++epoch) {
         // a3-a5
         trace_phase.reset(new NvtxRange("a3-a6 keys, sort, gather, start levels"));
-        uint64_t *keys = sc.get<uint64_t>("keys", n), *kalt = sc.get<uint64_t>("keys_alt", n);
-        uint32_t *perm = sc.get<uint32_t>("perm", n), *palt = sc.get<uint32_t>("perm_alt", n);
-        k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
-        radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
-        float *xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
-        k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
+        uint64_t *keys = res_keys;
+        uint32_t *perm = res_perm;
+        float *xsort = res_xsort;
+        if (rmode != 2) {
+            uint64_t *kalt = sc.get<uint64_t>("keys_alt", n);
+            uint32_t *palt = sc.get<uint32_t>("perm_alt", n);
+            keys = sc.get<uint64_t>("keys", n);
+            perm = sc.get<uint32_t>("perm", n);
+            k_keys<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, gp, keys, perm); ++launches;
+            radix_sort<uint64_t>(keys, perm, kalt, palt, n, hp.key_bits);
+            xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
+            k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
+        }
+        if (rmode == 1) {
+            // resident index built: keep the data side and stop (no queries)
+            CK(cudaGetLastError());
+            res_keys = keys;
+            res_perm = perm;
+            res_xsort = xsort;
+            res_hp = hp;
+            res_wm = stats.width_mult;
+            for (auto &t : res_tabs) t = LevelTab{};
+            CK(cudaEventRecord(ev[1], s));
+            CK(cudaEventRecord(ev[2], s));
+            CK(cudaStreamSynchronize(s));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[0], ev[2]));
+            stats.ms_total = ms;
+            stats.ms_index = ms;
+            stats.launches = launches;
+            return;
+        }
         // queries: keys on the data grid, sorted, gathered (the data arrays for a self-join)
         uint64_t *qkeys = keys;
         uint32_t *qperm = perm;
@@ -681,13 +750,10 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         const int QM = E2 <= 4 ? 16 : 8;
         const size_t smem2 = scan2_smem_bytes(d, QM, E2);
 
-        // per-level cell hash maps, built on first use
-        struct LevelTab {
-            uint4 *slot = nullptr;
-            uint32_t mask = 0;
-            bool built = false;
-        };
-        LevelTab tabs[MAX_LEVELS];
+        // per-level cell hash maps, built on first use (a resident index
+        // keeps its maps from one call to the next)
+        LevelTab local_tabs[MAX_LEVELS];
+        LevelTab *tabs = rmode == 2 ? res_tabs : local_tabs;
         auto build_level = [&](int L) {
             if (tabs[L].built) return;
             const int shift = d * L;
@@ -1020,7 +1086,39 @@ struct knnjoin_ctx {
     size_t budget = 0, in_use = 0;
     std::mutex big_token;  // see Pipeline::big_token
     TuneTable tune;
+    std::vector<knnjoin_index *> indexes;  // live resident indexes (under g_idx_mu)
+    std::mutex err_mu;                     // index queries writing err
 };
+
+// Resident index: one data set indexed once on its own pipeline (stream and
+// scratch), answering R x S queries until destroyed.
+struct knnjoin_index {
+    knnjoin_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    Pipeline pipe;
+    std::mutex mu;  // one query at a time
+    std::string err;
+    int64_t n = 0;
+    int d = 0;
+    int K = 0;
+};
+
+// Every live index of every context, so that destroying an index twice (or
+// after its context) is detected without touching freed memory.
+static std::mutex g_idx_mu;
+static std::set<knnjoin_index *> g_idx_live;
+
+static void index_free(knnjoin_index *ix)
+{
+    cudaSetDevice(ix->ctx->device);
+    if (ix->stream) {
+        cudaStreamSynchronize(ix->stream);
+        ix->pipe.release();
+        cudaStreamSynchronize(ix->stream);
+        cudaStreamDestroy(ix->stream);
+    }
+    delete ix;
+}
 
 // Device memory a join of n points holds while it runs (an estimate: the
 // scratch of one pipeline, two levels of cell maps, and staging copies of
@@ -1118,20 +1216,23 @@ static void start_workers(knnjoin_ctx *ctx)
     }
 }
 
-static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f)
+// Run f, map its exception to a status and put the message in the
+// context's error string (or in *msg when given).
+static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f, std::string *msg = nullptr)
 {
+    std::string *err = msg ? msg : (ctx ? &ctx->err : nullptr);
     try {
         f();
-        if (ctx) ctx->err.clear();
+        if (err) err->clear();
         return KNN_OK;
     } catch (const KnnError &e) {
-        if (ctx) ctx->err = e.msg;
+        if (err) *err = e.msg;
         return e.st;
     } catch (const std::bad_alloc &) {
-        if (ctx) ctx->err = "host allocation failed";
+        if (err) *err = "host allocation failed";
         return KNN_ERR_NOMEM;
     } catch (const std::exception &e) {
-        if (ctx) ctx->err = e.what();
+        if (err) *err = e.what();
         return KNN_ERR_INVALID;
     }
 }
@@ -1223,6 +1324,14 @@ void knnjoin_destroy(knnjoin_ctx *ctx)
         if (w->th.joinable()) w->th.join();
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    {
+        std::lock_guard<std::mutex> lk(g_idx_mu);
+        for (knnjoin_index *ix : ctx->indexes) {
+            g_idx_live.erase(ix);
+            index_free(ix);
+        }
+        ctx->indexes.clear();
+    }
     for (auto &w : ctx->workers) {
         cudaStreamSynchronize(w->stream);
         w->pipe.release();
@@ -1254,6 +1363,90 @@ knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, 
         validate_join(queries, nq, points, n, d, K, out_ids, out_dist);
         ctx->main.run(points, n, d, K, out_ids, out_dist, queries, nq);
     });
+}
+
+knnjoin_status knnjoin_index_create(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                    knnjoin_index **out)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    if (out) *out = nullptr;
+    knnjoin_index *ix = nullptr;
+    knnjoin_status st = guard(ctx, [&] {
+        if (!points || !out) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        CK(cudaSetDevice(ctx->device));
+        ix = new knnjoin_index();
+        ix->ctx = ctx;
+        ix->n = n;
+        ix->d = d;
+        ix->K = K;
+        CK(cudaStreamCreateWithFlags(&ix->stream, cudaStreamNonBlocking));
+        ix->pipe.init(ctx->device, ix->stream, &ctx->al);
+        ix->pipe.width_mult = ctx->main.width_mult;
+        ix->pipe.tune = &ctx->tune;
+        // work queued on the context's stream (the points' producer) first
+        CK(cudaEventRecord(ctx->main.ev[0], ctx->stream));
+        CK(cudaStreamWaitEvent(ix->stream, ctx->main.ev[0], 0));
+        ix->pipe.res_mode = 1;
+        ix->pipe.run(points, n, d, K, nullptr, nullptr);
+        ix->pipe.res_mode = 2;
+    });
+    if (st != KNN_OK) {
+        if (ix) index_free(ix);
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_idx_mu);
+        ctx->indexes.push_back(ix);
+        g_idx_live.insert(ix);
+    }
+    *out = ix;
+    return KNN_OK;
+}
+
+knnjoin_status knnjoin_index_query(knnjoin_index *ix, const float *queries, int64_t nq, int K,
+                                   int32_t *out_ids, double *out_dist)
+{
+    if (!ix) return KNN_ERR_INVALID;
+    knnjoin_ctx *ctx = ix->ctx;
+    std::lock_guard<std::mutex> lk(ix->mu);
+    // queries of different indexes may run on several threads: the message
+    // of a failure goes to the context under its lock, success leaves it
+    knnjoin_status st = guard(nullptr, [&] {
+        validate_join(queries, nq, queries, ix->n, ix->d, K, out_ids, out_dist);
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaEventRecord(ix->pipe.ev[0], ctx->stream));
+        CK(cudaStreamWaitEvent(ix->stream, ix->pipe.ev[0], 0));
+        ix->pipe.run(nullptr, ix->n, ix->d, K, out_ids, out_dist, queries, nq);
+        // results are complete; later work on the context's stream may use them
+        CK(cudaEventRecord(ix->pipe.ev[2], ix->stream));
+        CK(cudaStreamWaitEvent(ctx->stream, ix->pipe.ev[2], 0));
+    }, &ix->err);
+    if (st != KNN_OK) {
+        std::lock_guard<std::mutex> elk(ctx->err_mu);
+        ctx->err = ix->err;
+    }
+    return st;
+}
+
+knnjoin_status knnjoin_index_stats(knnjoin_index *ix, knnjoin_stats *out)
+{
+    if (!ix || !out) return KNN_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(ix->mu);
+    *out = ix->pipe.stats;
+    return KNN_OK;
+}
+
+void knnjoin_index_destroy(knnjoin_index *ix)
+{
+    std::lock_guard<std::mutex> lk(g_idx_mu);
+    if (!g_idx_live.erase(ix)) return;  // not a live index
+    auto &v = ix->ctx->indexes;
+    v.erase(std::remove(v.begin(), v.end(), ix), v.end());
+    {
+        std::lock_guard<std::mutex> wait_query(ix->mu);
+    }
+    index_free(ix);
 }
 
 knnjoin_status knnjoin_autotune(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
@@ -1390,6 +1583,60 @@ knnjoin_status knnjoin_get_stats(knnjoin_ctx *ctx, uint64_t job_id, knnjoin_stat
     }
     *out = it->second->stats;
     return KNN_OK;
+}
+
+knnjoin_status knnjoin_fp32_mismatch(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                     const int32_t *ids, const int64_t *rows, int64_t nrows,
+                                     int64_t *out_counts)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!points || !ids || !rows || !out_counts) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        if (nrows < 1 || nrows > 2147483647LL) fail(KNN_ERR_INVALID, "nrows must be in [1, 2^31 - 1]");
+        if (is_device_ptr(rows)) fail(KNN_ERR_INVALID, "rows must be host memory");
+        for (int64_t r = 0; r < nrows; ++r)
+            if (rows[r] < 0 || rows[r] >= n) fail(KNN_ERR_INVALID, "row index out of range");
+        Pipeline &P = ctx->main;
+        CK(cudaSetDevice(P.device));
+        const float *pts = points;
+        if (!is_device_ptr(points)) {
+            float *p = P.sc.get<float>("diag_pts", (size_t)n * d);
+            CK(cudaMemcpyAsync(p, points, sizeof(float) * n * d, cudaMemcpyHostToDevice, P.s));
+            pts = p;
+        }
+        const int32_t *idd = ids;
+        if (!is_device_ptr(ids)) {
+            int32_t *p = P.sc.get<int32_t>("diag_ids", (size_t)n * K);
+            CK(cudaMemcpyAsync(p, ids, sizeof(int32_t) * n * K, cudaMemcpyHostToDevice, P.s));
+            idd = p;
+        }
+        int64_t *rowd = P.sc.get<int64_t>("diag_rows", (size_t)nrows);
+        uint32_t *outd = P.sc.get<uint32_t>("diag_out", (size_t)nrows * 2);
+        std::vector<uint32_t> outh((size_t)nrows * 2);
+        CK(cudaMemcpyAsync(rowd, rows, sizeof(int64_t) * nrows, cudaMemcpyHostToDevice, P.s));
+        const unsigned grid = (unsigned)std::min<int64_t>(nrows, (int64_t)P.nsm * 8);
+        switch (d) {
+#define KNN_RANK_CASE(D) \
+    case D: k_fp32_rank<D><<<grid, RANK_CTA, 0, P.s>>>(pts, n, K, idd, rowd, nrows, outd); break;
+            KNN_RANK_CASE(1) KNN_RANK_CASE(2) KNN_RANK_CASE(3) KNN_RANK_CASE(4)
+            KNN_RANK_CASE(5) KNN_RANK_CASE(6) KNN_RANK_CASE(7) KNN_RANK_CASE(8)
+#undef KNN_RANK_CASE
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(outh.data(), outd, sizeof(uint32_t) * nrows * 2, cudaMemcpyDeviceToHost, P.s));
+        CK(cudaStreamSynchronize(P.s));
+        int64_t rows_wrong = 0, wrong = 0, missing = 0;
+        for (int64_t r = 0; r < nrows; ++r) {
+            if (outh[2 * r] == 0xffffffffu) fail(KNN_ERR_INVALID, "ids row holds an index outside [0, n) or the row itself");
+            rows_wrong += outh[2 * r] != 0;
+            wrong += outh[2 * r];
+            missing += outh[2 * r + 1];
+        }
+        out_counts[0] = rows_wrong;
+        out_counts[1] = wrong;
+        out_counts[2] = missing;
+    });
 }
 
 const char *knnjoin_last_error(knnjoin_ctx *ctx)
