@@ -707,6 +707,111 @@ def run_join(args, rank, world, local_rank):
     return 0
 
 
+def run_index(args, rank, world, local_rank):
+    """Resident index: for each d in {2, 4, 6}, 2M uniform points indexed once
+    (knnjoin_index_create, untimed) and kept on the device; one step = one
+    batch of uniform query points per d through knnjoin_index_query, K = 32.
+    The same batches through knnjoin_join (index rebuilt per batch) are timed
+    beside it; sampled rows are checked against the oracle's brute force."""
+    import torch
+    import paper_1810_04758_b300 as kj
+    from paper_1810_04758_b300 import build as kbuild
+
+    kbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    K, n, B = 32, 2_000_000, args.batch
+    nb = args.steps + args.warmup
+    stream = torch.cuda.current_stream(dev)
+    ctx = kj.Context(device=local_rank, stream=stream)
+    sets = {}
+    for d in (2, 4, 6):
+        p = gen.make_points("uniform", n, d, seed=0, name=f"unif{d}d_2m")
+        q = gen.make_points("uniform", nb * B, d, seed=2, name=f"index_queries_{d}d")
+        tp = torch.from_numpy(p).to(dev)
+        t0 = time.perf_counter()
+        ix = ctx.index(tp, K)
+        torch.cuda.synchronize()
+        build_ms = ix.stats()["ms_total"]
+        sets[d] = dict(p=p, q=q, tp=tp, tq=torch.from_numpy(q).to(dev), ix=ix, build_ms=build_ms,
+                       build_wall_ms=(time.perf_counter() - t0) * 1e3,
+                       oi=torch.empty((B, K), dtype=torch.int32, device=dev),
+                       od=torch.empty((B, K), dtype=torch.float64, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def batch(v, i):
+        return v["tq"][i * B:(i + 1) * B]
+
+    def timed(fn):
+        for i in range(args.warmup):
+            fn(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = []
+        for i in range(args.warmup, nb):
+            flush.fill_(float(i))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(i)
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        return ms
+
+    def via_index(i):
+        for v in sets.values():
+            v["ix"].query(batch(v, i), K, v["oi"], v["od"])
+
+    def via_join(i):
+        for v in sets.values():
+            ctx.join(batch(v, i), v["tp"], K, v["oi"], v["od"])
+
+    with ClockSampler(local_rank) as clk:
+        ms_ix = timed(via_index)
+        ms_join = timed(via_join)
+    total = max_over_ranks(sum(ms_ix), dev, world)
+    total_join = max_over_ranks(sum(ms_join), dev, world)
+    # the last batch: resident index against the oracle on sampled rows
+    checked = 0
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        via_index(nb - 1)
+        torch.cuda.synchronize()
+        for d, v in sets.items():
+            rows = np.linspace(0, B - 1, 64).astype(np.int64)
+            q = v["q"][(nb - 1) * B:nb * B]
+            wi, wd = oracle.bf_rs(q[rows], v["p"], K)
+            assert np.array_equal(v["oi"].cpu().numpy()[rows], wi)
+            assert np.array_equal(v["od"].cpu().numpy()[rows], wd)
+            checked += len(rows)
+    per_d = {f"{d}d": {"index_build_ms": round(v["build_ms"], 3)} for d, v in sets.items()}
+    for v in sets.values():
+        v["ix"].close()
+    ctx.close()
+    if rank != 0:
+        return 0
+    ms_step, ms_step_join = total / args.steps, total_join / args.steps
+    line = {
+        "metric": f"query points/s against a resident 2M-point index (K=32, batches of {B}, 2-6D)",
+        "value": world * 3 * B / (ms_step / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (scan) + exact canonical-f64 re-score", "data": "synthetic",
+        "config": {"workload": f"resident index: d in {{2,4,6}}, 2M uniform points (seed 0) indexed once; "
+                               f"one step = one batch of {B} uniform queries (stream 2) per d, K=32, "
+                               f"knnjoin_index_query",
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "join_per_batch": {"value": world * 3 * B / (ms_step_join / 1e3), "ms_per_step": ms_step_join,
+                           "api": "knnjoin_join on the same batches (index rebuilt per batch)"},
+        "speedup_vs_join": ms_step_join / ms_step,
+        "per_d": per_d,
+        "rows_checked_against_oracle": checked,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_served(args, rank, world, local_rank):
     import torch
     import paper_1810_04758_b300 as kj
@@ -801,8 +906,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "join"], default="unif")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "join", "index"],
+                    default="unif")
     ap.add_argument("--jobs", type=int, default=0, help="batched/served: number of joins")
+    ap.add_argument("--batch", type=int, default=16384, help="index: query points per batch")
     ap.add_argument("--workers", type=int, default=0, help="batched/served: worker pipelines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -826,23 +933,19 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if args.workload in ("batched", "served"):
+        if args.workload not in WORKLOADS:
             print(json.dumps({"impl": "reference", "unavailable":
                               "the CPU oracle is timed on the unif/expo workloads only"}))
             return 0
         return run_reference(args, rank, world)
-    if args.workload == "batched":
-        return run_batched(args, rank, world, local_rank)
-    if args.workload == "served":
-        return run_served(args, rank, world, local_rank)
-    if args.workload == "join":
-        return run_join(args, rank, world, local_rank)
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    runner = {"batched": run_batched, "served": run_served, "join": run_join,
+              "index": run_index}.get(args.workload, run_ours)
     try:
-        return run_ours(args, rank, world, local_rank)
+        return runner(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch
