@@ -707,6 +707,82 @@ def run_join(args, rank, world, local_rank):
     return 0
 
 
+def run_sharded(args, rank, world, local_rank):
+    """One join split over the ranks by query rows (--shard): each rank
+    indexes all points and computes its row range of every join of the
+    workload (shard_rows, knnjoin_self_join_rows); the total work is fixed,
+    so this is strong scaling.  At N = 1 it is the step as blocking calls."""
+    import torch
+    import paper_1810_04758_b300 as kj
+    from paper_1810_04758_b300 import build as kbuild
+
+    kbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = kj.Context(device=local_rank, stream=stream, tune_cache_path=args.tune_cache or None)
+    names = WORKLOADS[args.workload]
+    hosts = {nm: gen.config_points(nm) for nm in names}
+    dpts = {nm: torch.from_numpy(p).to(dev) for nm, (p, K) in hosts.items()}
+    ranges = {nm: kj.shard_rows(len(p), world, rank) for nm, (p, K) in hosts.items()}
+    outs = {nm: (torch.empty((e - b, hosts[nm][1]), dtype=torch.int32, device=dev),
+                 torch.empty((e - b, hosts[nm][1]), dtype=torch.float64, device=dev))
+            for nm, (b, e) in ranges.items()}
+    if not args.no_autotune:
+        cached = tune_cache_keys(args.tune_cache)
+        for nm in names:
+            n_, d_ = hosts[nm][0].shape
+            if (d_, hosts[nm][1], int(n_).bit_length() - 1) not in cached:
+                ctx.autotune(dpts[nm], hosts[nm][1])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        launches = 0
+        for nm in names:
+            ctx.self_join_rows(dpts[nm], hosts[nm][1], *ranges[nm], *outs[nm])
+            launches += ctx.stats()["launches"]
+        return launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms, launches = [], 0
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            launches += step()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+    if world > 1:
+        torch.distributed.barrier()
+    total = max_over_ranks(sum(ms), dev, world)
+    ctx.close()
+    if rank != 0:
+        return 0
+    ms_step = total / args.steps
+    nq_step = sum(len(p) for p, _ in hosts.values())
+    line = {
+        "metric": METRIC if args.workload == "unif" else METRIC.replace("K=32", "K=64"),
+        "value": nq_step / (ms_step / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32 (scan) + exact canonical-f64 re-score", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "n": 2_000_000, "d": [2, 4, 6],
+                   "K": hosts[names[0]][1], "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"row shards x{world} (each rank: full index, its rows)"},
+        "gpu_launches": launches,
+        "step_api": "knnjoin_self_join_rows, one shard of each join per rank, blocking calls",
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_index(args, rank, world, local_rank):
     """Resident index: for each d in {2, 4, 6}, 2M uniform points indexed once
     (knnjoin_index_create, untimed) and kept on the device; one step = one
@@ -910,6 +986,9 @@ def main():
                     default="unif")
     ap.add_argument("--jobs", type=int, default=0, help="batched/served: number of joins")
     ap.add_argument("--batch", type=int, default=16384, help="index: query points per batch")
+    ap.add_argument("--shard", action="store_true",
+                    help="unif/expo: split each join over the ranks by query rows (strong scaling) "
+                         "instead of running replicas")
     ap.add_argument("--workers", type=int, default=0, help="batched/served: worker pipelines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -943,7 +1022,7 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     runner = {"batched": run_batched, "served": run_served, "join": run_join,
-              "index": run_index}.get(args.workload, run_ours)
+              "index": run_index}.get(args.workload, run_sharded if args.shard else run_ours)
     try:
         return runner(args, rank, world, local_rank)
     finally:

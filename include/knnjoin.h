@@ -160,6 +160,18 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
 knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, const float *points, int64_t n,
                             int d, int K, int32_t *out_ids, double *out_dist);
 
+/* One shard of a self-join: the rows [row_begin, row_end) of the result of
+ * knnjoin_self_join on the same points (bit for bit), written to out_ids /
+ * out_dist of row_end - row_begin rows (row r of the shard is point
+ * row_begin + r).  Queries are independent given all points, so a join is
+ * split over GPUs by giving each its own row range: each GPU indexes all n
+ * points (deterministic, so every GPU builds the same index) and answers its
+ * rows, with no exchange between GPUs (the paper's future-work note on
+ * multi-GPU joins, Sec. 6, Discussion and Conclusions).  0 <= row_begin < row_end <= n, else
+ * KNN_ERR_INVALID; other rules as knnjoin_self_join. */
+knnjoin_status knnjoin_self_join_rows(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                      int64_t row_begin, int64_t row_end, int32_t *out_ids, double *out_dist);
+
 /* Resident index: index a data set once and keep it on the device, then
  * answer R x S queries against it (the same result as knnjoin_join with these
  * points: for each query row the K nearest data rows under (D, j), nothing

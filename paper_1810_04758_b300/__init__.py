@@ -34,7 +34,7 @@ EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_jo
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc",
            "knnjoin_fp32_mismatch", "knnjoin_index_create", "knnjoin_index_query",
-           "knnjoin_index_stats", "knnjoin_index_destroy")
+           "knnjoin_index_stats", "knnjoin_index_destroy", "knnjoin_self_join_rows")
 KNN_NOALLOC_MAX_POINTS = 65536
 
 
@@ -113,6 +113,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_fp32_mismatch.argtypes = [P, P, I64, I, I, P, ctypes.POINTER(ctypes.c_int64), I64,
                                           ctypes.POINTER(ctypes.c_int64)]
     lib.knnjoin_fp32_mismatch.restype = I
+    lib.knnjoin_self_join_rows.argtypes = [P, P, I64, I, I, I64, I64, P, P]
+    lib.knnjoin_self_join_rows.restype = I
     lib.knnjoin_index_create.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.knnjoin_index_create.restype = I
     lib.knnjoin_index_query.argtypes = [P, P, I64, I, P, P]
@@ -195,6 +197,12 @@ def knnjoin_fp32_mismatch(ctx: int, points: int, n: int, d: int, K: int, ids: in
     return int(out[0]), int(out[1]), int(out[2])
 
 
+def knnjoin_self_join_rows(ctx: int, points: int, n: int, d: int, K: int, row_begin: int, row_end: int,
+                           out_ids: int, out_dist: int) -> int:
+    return _check(ctx, load_library().knnjoin_self_join_rows(ctx, points, n, d, K, row_begin, row_end,
+                                                             out_ids, out_dist))
+
+
 def knnjoin_index_create(ctx: int, points: int, n: int, d: int, K: int) -> int:
     out = ctypes.c_void_p(0)
     _check(ctx, load_library().knnjoin_index_create(ctx, points, n, d, K, ctypes.byref(out)))
@@ -254,6 +262,15 @@ def knnjoin_get_stats(ctx: int, job_id: int = 0) -> dict:
     st = KnnjoinStats()
     _check(ctx, load_library().knnjoin_get_stats(ctx, job_id, ctypes.byref(st)))
     return st.as_dict()
+
+
+def shard_rows(n: int, world: int, rank: int) -> tuple[int, int]:
+    """Row range [begin, end) of rank `rank` when a join of n query rows is
+    split over `world` GPUs: contiguous, disjoint, covering [0, n), sizes
+    differing by at most one (queries of random order cost alike on average)."""
+    if world < 1 or not 0 <= rank < world or n < world:
+        raise ValueError("need 0 <= rank < world <= n")
+    return n * rank // world, n * (rank + 1) // world
 
 
 # ---------------------------------------------------------------------------
@@ -328,6 +345,20 @@ class Context:
         out_ids, out_dist = self._outputs(n, K, points, out_ids, out_dist)
         knnjoin_self_join(self.ctx, points.data_ptr(), n, d, K, out_ids.data_ptr(),
                           out_dist.data_ptr())
+        return out_ids, out_dist
+
+    def self_join_rows(self, points, K: int, row_begin: int, row_end: int, out_ids=None, out_dist=None):
+        """Rows [row_begin, row_end) of the self-join of `points` (one shard of
+        the join): (ids int32 [rows, K], dist float64 [rows, K])."""
+        torch = self._torch
+        if points.dtype != torch.float32 or points.dim() != 2:
+            raise ValueError("points must be a float32 [n, d] tensor")
+        points = points.contiguous()
+        n, d = points.shape
+        rows = max(0, row_end - row_begin)
+        out_ids, out_dist = self._outputs(max(rows, 1), K, points, out_ids, out_dist)
+        knnjoin_self_join_rows(self.ctx, points.data_ptr(), n, d, K, row_begin, row_end, out_ids.data_ptr(),
+                               out_dist.data_ptr())
         return out_ids, out_dist
 
     def autotune(self, points, K: int) -> float:

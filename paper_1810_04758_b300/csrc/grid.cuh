@@ -628,13 +628,13 @@ __global__ void k_mark_done(const uint32_t *__restrict__ list, const uint32_t *_
     }
 }
 
-// Chunked output: flag the sorted query positions whose original row lies in
-// [r0, r1).
-__global__ void k_row_flags(const uint32_t *__restrict__ qperm, int64_t nq, uint32_t r0, uint32_t r1,
-                            uint32_t *__restrict__ flags)
+// Chunked or sharded output: flags[a] = (the original row of sorted query
+// position list[a] lies in [r0, r1)).
+__global__ void k_row_flags(const uint32_t *__restrict__ list, const uint32_t *__restrict__ qperm, int64_t m,
+                            uint32_t r0, uint32_t r1, uint32_t *__restrict__ flags)
 {
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nq; a += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = qperm[a];
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = qperm[list[a]];
         flags[a] = r >= r0 && r < r1;
     }
 }

@@ -345,9 +345,10 @@ struct Pipeline {
     }
 
     // self-join of the n points, or (qry_in != null) the K nearest of the n
-    // points for each of the nq query points
+    // points for each of the nq query points; only query rows [row_b, row_e)
+    // (row_e < 0: all) are computed, into outputs of row_e - row_b rows
     void run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
-             const float *qry_in = nullptr, int64_t nq_in = 0);
+             const float *qry_in = nullptr, int64_t nq_in = 0, int64_t row_b = 0, int64_t row_e = -1);
 };
 
 __global__ void k_init_reduce(PrepReduce *r)
@@ -494,24 +495,27 @@ void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
 }
 
 void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
-                   const float *qry_in, int64_t nq_in)
+                   const float *qry_in, int64_t nq_in, int64_t row_b, int64_t row_e)
 {
     NvtxRange trace_join(qry_in ? "knnjoin: R x S join" : "knnjoin: self-join");
     const bool self = qry_in == nullptr;
     const int64_t nq = self ? n : nq_in;  // queries (output rows)
     const int rmode = res_mode;           // 1: build a resident index, 2: query one
+    if (row_e < 0) row_e = nq;
+    const int64_t nrows = row_e - row_b;  // output rows (a shard of the queries, or all)
+    const bool sharded = nrows < nq;
     CK(cudaSetDevice(device));
     const bool pts_dev = is_device_ptr(pts_in);
     const bool ids_dev = is_device_ptr(ids_in);
     const bool dist_dev = is_device_ptr(dist_in);
     // large joins whose results go to host memory take turns (see big_token)
     std::unique_lock<std::mutex> turn;
-    if (big_token && !(ids_dev && dist_dev) && nq * (int64_t)K >= BIG_JOB_ENTRIES)
+    if (big_token && !(ids_dev && dist_dev) && nrows * (int64_t)K >= BIG_JOB_ENTRIES)
         turn = std::unique_lock<std::mutex>(*big_token);
     memset(&stats, 0, sizeof(stats));
     launches = 0;
     double ms_scan = 0.0;
-    stats.n = nq;
+    stats.n = nrows;
     stats.d = d;
     stats.K = K;
 
@@ -533,22 +537,24 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // results bound for host memory that would not fit on the device (or
     // exceed out_chunk_bytes) are computed in chunks of query rows, each
     // copied out before the next
-    int64_t chunk_rows = nq;
+    int64_t chunk_rows = nrows;
     if (policy == 0 && rmode != 1 && !(ids_dev && dist_dev)) {
         const size_t row_bytes = (size_t)K * (sizeof(int32_t) + sizeof(double));
         size_t limit = out_chunk_bytes;
         if (limit == 0) {
             size_t freeb = 0, totalb = 0;
             CK(cudaMemGetInfo(&freeb, &totalb));
-            if ((size_t)nq * row_bytes > freeb / 2) limit = freeb / 4;
+            if ((size_t)nrows * row_bytes > freeb / 2) limit = freeb / 4;
         }
-        if (limit > 0 && (size_t)nq * row_bytes > limit)
+        if (limit > 0 && (size_t)nrows * row_bytes > limit)
             chunk_rows = std::max<int64_t>(1, (int64_t)(limit / row_bytes));
     }
-    const bool chunked = chunk_rows < nq;
-    stats.chunks = (nq + chunk_rows - 1) / chunk_rows;
-    int32_t *ids = ids_dev || rmode == 1 ? ids_in : sc.get<int32_t>("ids_out", (size_t)chunk_rows * K);
-    double *dist = dist_dev || rmode == 1 ? dist_in : sc.get<double>("dist_out", (size_t)chunk_rows * K);
+    const bool chunked = chunk_rows < nrows;
+    stats.chunks = (nrows + chunk_rows - 1) / chunk_rows;
+    // chunks go through scratch buffers (both outputs), whole results straight
+    // to device outputs
+    int32_t *ids = !chunked && (ids_dev || rmode == 1) ? ids_in : sc.get<int32_t>("ids_out", (size_t)chunk_rows * K);
+    double *dist = !chunked && (dist_dev || rmode == 1) ? dist_in : sc.get<double>("dist_out", (size_t)chunk_rows * K);
     CK(cudaEventRecord(ev[0], s));
 
     // a1
@@ -809,8 +815,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             return cntv;
         };
 
-        for (int64_t r0 = 0; r0 < nq; r0 += chunk_rows) {
-            const int64_t r1 = std::min(nq, r0 + chunk_rows);
+        for (int64_t r0 = row_b; r0 < row_e; r0 += chunk_rows) {
+            const int64_t r1 = std::min(row_e, r0 + chunk_rows);
             k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
             m = nq;
             if (policy == 1 && epoch > 0) {
@@ -824,16 +830,18 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
                 std::swap(active, active2);
             }
-            if (chunked) {
-                // this chunk's queries: original rows [r0, r1)
-                k_row_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, nq, (uint32_t)r0, (uint32_t)r1, flags); ++launches;
-                scan(flags, rid, nq);
-                fetch(pinned, rid + nq - 1, 4);
-                fetch(pinned + 1, flags + nq - 1, 4);
+            if ((chunked || sharded) && m > 0) {
+                // this chunk's queries: the entries of the active list (all
+                // queries, or those not done yet) whose original row is in [r0, r1)
+                k_row_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, qperm, m, (uint32_t)r0, (uint32_t)r1, flags); ++launches;
+                scan(flags, rid, m);
+                fetch(pinned, rid + m - 1, 4);
+                fetch(pinned + 1, flags + m - 1, 4);
                 CK(cudaStreamSynchronize(s));
-                m = (int64_t)pinned[0] + pinned[1];
-                k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
+                const int64_t mr = (int64_t)pinned[0] + pinned[1];
+                k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, flags, rid, m, active2); ++launches;
                 std::swap(active, active2);
+                m = mr;
             }
             row0 = r0;
             while (m > 0) {
@@ -868,7 +876,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.self = self ? 1 : 0;
                 a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
                 a.row0 = row0;
-                a.out_rows = chunked ? chunk_rows : nq;
+                a.out_rows = chunked ? chunk_rows : nrows;
                 a.nq = nq;
                 a.counter = small + 3;
                 for (int L = 0; L < MAX_LEVELS; ++L) {
@@ -950,8 +958,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             if (chunked) {
                 const int64_t rows = r1 - r0;
                 k_sqrt_rows<<<grid_for(rows * K, 256, nsm, 16), 256, 0, s>>>(dist, rows * K); ++launches;
-                CK(cudaMemcpyAsync(ids_in + r0 * K, ids, sizeof(int32_t) * rows * K, cudaMemcpyDeviceToHost, s));
-                CK(cudaMemcpyAsync(dist_in + r0 * K, dist, sizeof(double) * rows * K, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(ids_in + (r0 - row_b) * K, ids, sizeof(int32_t) * rows * K, cudaMemcpyDefault, s));
+                CK(cudaMemcpyAsync(dist_in + (r0 - row_b) * K, dist, sizeof(double) * rows * K, cudaMemcpyDefault, s));
             }
         }
         if (policy != 1 || m == 0) break;
@@ -965,15 +973,15 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.start_level = first_level;
     stats.passes = pass;
     if (!chunked) {
-        k_sqrt_rows<<<grid_for(nq * K, 256, nsm, 16), 256, 0, s>>>(dist, nq * K); ++launches;
+        k_sqrt_rows<<<grid_for(nrows * K, 256, nsm, 16), 256, 0, s>>>(dist, nrows * K); ++launches;
     }
     CK(cudaEventRecord(ev[2], s));
     if (turn.owns_lock()) {
         CK(cudaEventSynchronize(ev[2]));
         turn.unlock();
     }
-    if (!ids_dev && !chunked) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s));
-    if (!dist_dev && !chunked) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * nq * K, cudaMemcpyDeviceToHost, s));
+    if (!ids_dev && !chunked) CK(cudaMemcpyAsync(ids_in, ids, sizeof(int32_t) * nrows * K, cudaMemcpyDeviceToHost, s));
+    if (!dist_dev && !chunked) CK(cudaMemcpyAsync(dist_in, dist, sizeof(double) * nrows * K, cudaMemcpyDeviceToHost, s));
     fetch(pinned, st, 4 * sizeof(unsigned long long));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
@@ -1352,6 +1360,18 @@ knnjoin_status knnjoin_self_join(knnjoin_ctx *ctx, const float *points, int64_t 
     return guard(ctx, [&] {
         validate(points, n, d, K, out_ids, out_dist);
         ctx->main.run(points, n, d, K, out_ids, out_dist);
+    });
+}
+
+knnjoin_status knnjoin_self_join_rows(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                      int64_t row_begin, int64_t row_end, int32_t *out_ids, double *out_dist)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        validate(points, n, d, K, out_ids, out_dist);
+        if (row_begin < 0 || row_begin >= row_end || row_end > n)
+            fail(KNN_ERR_INVALID, "rows must satisfy 0 <= row_begin < row_end <= n");
+        ctx->main.run(points, n, d, K, out_ids, out_dist, nullptr, 0, row_begin, row_end);
     });
 }
 

@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
             }
             if (certified) {
                 const int64_t rowq = (int64_t)a.qperm[qs] - a.row0;
-                const bool rowok = KNN_GUARD(rowq >= 0 && rowq < a.out_rows, 9);
+                const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
+                const bool rowok = KNN_GUARD(rowin, 9) && rowin;
                 const int64_t row = rowq * K;
                 for (int u = 0; u < mine; ++u)
                     if (rr[u] < (uint32_t)K && rowok) {

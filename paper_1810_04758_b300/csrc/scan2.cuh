@@ -920,7 +920,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 if (certified) {
                     flag = 0;
                     const int64_t rowq = (int64_t)a.qperm[qsv[i]] - a.row0;
-                    const bool rowok = KNN_GUARD(rowq >= 0 && rowq < a.out_rows, 5);
+                    const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
+                    const bool rowok = KNN_GUARD(rowin, 5) && rowin;
                     const int64_t row = rowq * K;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
