@@ -446,7 +446,7 @@ void ensure_nb_order(int dev)
     done[dev & 63] = true;
 }
 
-template <int DIM, int E>
+template <int DIM, int E, bool MEGA>
 void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
 {
     ensure_nb_order(P.device);
@@ -454,42 +454,46 @@ void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
     static bool configured[64] = {};
     int dev = P.device;
     if (!configured[dev & 63]) {
-        CK(cudaFuncSetAttribute(k_scan2<DIM, QM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        CK(cudaFuncSetAttribute(k_scan2<DIM, QM, E, MEGA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         configured[dev & 63] = true;
     }
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan2<DIM, QM, E>, S2_CTA, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan2<DIM, QM, E, MEGA>, S2_CTA, smem));
     if (occ < 1) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
     unsigned grid = (unsigned)std::min<int64_t>(((int64_t)a.nitems + S2_WARPS - 1) / S2_WARPS,
                                                 (int64_t)occ * P.nsm);
     if (grid == 0) return;
-    k_scan2<DIM, QM, E><<<grid, S2_CTA, smem, P.s>>>(a);
+    k_scan2<DIM, QM, E, MEGA><<<grid, S2_CTA, smem, P.s>>>(a);
     ++P.launches;
     CK(cudaGetLastError());
 }
 
 template <int DIM>
-void dispatch_scan2_e(Pipeline &P, int E, const ScanArgs &a, size_t smem)
+void dispatch_scan2_e(Pipeline &P, int E, bool mega, const ScanArgs &a, size_t smem)
 {
-    switch (E) {
-    case 2: launch_scan2<DIM, 2>(P, a, smem); break;
-    case 4: launch_scan2<DIM, 4>(P, a, smem); break;
-    case 8: launch_scan2<DIM, 8>(P, a, smem); break;
+    switch (E * 2 + (mega ? 1 : 0)) {
+    case 4: launch_scan2<DIM, 2, false>(P, a, smem); break;
+    case 5: launch_scan2<DIM, 2, true>(P, a, smem); break;
+    case 8: launch_scan2<DIM, 4, false>(P, a, smem); break;
+    case 9: launch_scan2<DIM, 4, true>(P, a, smem); break;
+    case 16: launch_scan2<DIM, 8, false>(P, a, smem); break;
+    case 17: launch_scan2<DIM, 8, true>(P, a, smem); break;
     default: fail(KNN_ERR_INVALID, "internal: bad buffer size");
     }
 }
 
-void dispatch_scan2(Pipeline &P, int d, int E, const ScanArgs &a, size_t smem)
+// mega: the long-run walk that skips mega-tiles (k_scan2's MEGA)
+void dispatch_scan2(Pipeline &P, int d, int E, bool mega, const ScanArgs &a, size_t smem)
 {
     switch (d) {
-    case 1: dispatch_scan2_e<1>(P, E, a, smem); break;
-    case 2: dispatch_scan2_e<2>(P, E, a, smem); break;
-    case 3: dispatch_scan2_e<3>(P, E, a, smem); break;
-    case 4: dispatch_scan2_e<4>(P, E, a, smem); break;
-    case 5: dispatch_scan2_e<5>(P, E, a, smem); break;
-    case 6: dispatch_scan2_e<6>(P, E, a, smem); break;
-    case 7: dispatch_scan2_e<7>(P, E, a, smem); break;
-    case 8: dispatch_scan2_e<8>(P, E, a, smem); break;
+    case 1: dispatch_scan2_e<1>(P, E, mega, a, smem); break;
+    case 2: dispatch_scan2_e<2>(P, E, mega, a, smem); break;
+    case 3: dispatch_scan2_e<3>(P, E, mega, a, smem); break;
+    case 4: dispatch_scan2_e<4>(P, E, mega, a, smem); break;
+    case 5: dispatch_scan2_e<5>(P, E, mega, a, smem); break;
+    case 6: dispatch_scan2_e<6>(P, E, mega, a, smem); break;
+    case 7: dispatch_scan2_e<7>(P, E, mega, a, smem); break;
+    case 8: dispatch_scan2_e<8>(P, E, mega, a, smem); break;
     default: fail(KNN_ERR_INVALID, "d out of range");
     }
 }
@@ -909,7 +913,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.nitems = nitems;
                 CK(cudaMemsetAsync(small + 3, 0, 4, s));
                 CK(cudaEventRecord(evs[0], s));
-                if (fast) dispatch_scan2(*this, d, E2, a, smem2);
+                // skewed data, or a re-queued pass: walk long runs by
+                // mega-tiles (a query's box may hold long runs far from it)
+                if (fast) dispatch_scan2(*this, d, E2, pass > 0 || hp.finer > 0, a, smem2);
                 else dispatch_scan(*this, d, a, smem1);
                 CK(cudaEventRecord(evs[1], s));
                 // the scan's time and candidate count, read after the pass's

@@ -12,7 +12,8 @@
 //       flattens the runs;
 //   a8  runs of at least S2_BIG points go first, in super-tiles of S2_SUPER
 //       consecutive sorted points, each tested per query against the box of
-//       its Morton prefix; the other runs are scanned two tiles at a time:
+//       its Morton prefix (groups of S2_MEGA super-tiles are tested first and
+//       skipped whole); the other runs are scanned two tiles at a time:
 //       lane t holds candidates t and t + 32, loads their coordinates once
 //       and scores them against every query in the tiles' masks (query rows
 //       broadcast from shared memory), so a candidate read serves up to QM
@@ -104,6 +105,13 @@ constexpr int S2_WARPS = 4;
 #endif
 #ifndef S2_SUPER
 #define S2_SUPER 128
+#endif
+// Super-tiles are visited in groups of S2_MEGA (a mega-tile): a group whose
+// key-range box no query of the item can use is skipped whole, so a query
+// whose neighbourhood holds long runs far from it pays one box test per
+// S2_MEGA * S2_SUPER points instead of one per S2_SUPER.
+#ifndef S2_MEGA
+#define S2_MEGA 32
 #endif
 
 // Smallest d whose tiles score two queries at a time.
@@ -562,7 +570,33 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
     }
 }
 
-template <int DIM, int QM, int E>
+// One super-tile [sb, se), one tile of 32 candidates per step.
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_super_tile(const ScanArgs &a, uint32_t sb, uint32_t se, uint32_t smask,
+                                                 uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K,
+                                                 int lane, unsigned long long &st_cand)
+{
+    for (uint32_t t0 = sb; t0 < se; t0 += 32) {
+        const bool valid = t0 + lane < se;
+        const uint32_t s = valid ? t0 + lane : 0u;
+        float c[DIM];
+        if (valid) {
+            load_point<DIM>(a.xsort, s, c);
+            st_cand += (unsigned long long)__popc(smask);
+        } else {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+        }
+        scan2_tile<DIM, E>(c, s, valid, smask, buf, qc, hist, my_cnt, K, lane);
+    }
+}
+
+// MEGA selects the long-run walk: false, every super-tile tested in turn
+// (uniform data: the code of the hot loop stays as compiled without it);
+// true, mega-tiles tested first and skipped whole, two tiles per step
+// (density skew and re-queued passes, where one query's box can hold long
+// runs far from it).
+template <int DIM, int QM, int E, bool MEGA>
 __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -732,27 +766,78 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 const int nst = (int)((ce - cb + S2_SUPER - 1) / S2_SUPER);
                 const uint32_t sq = qsv[0];
                 const int u0 = (a.self && sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
-                for (int j = 0, left = nst; left > 0; ++j) {
-                    const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
-                    if (u < 0 || u >= nst) continue;
-                    --left;
-                    const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
-                    const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
-                    const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
-                    if (!smask) continue;
-                    for (uint32_t t0 = sb; t0 < se; t0 += 32) {
-                        const bool valid = t0 + lane < se;
-                        const uint32_t s = valid ? t0 + lane : 0u;
-                        float c[DIM];
-                        if (valid) {
-                            load_point<DIM>(a.xsort, s, c);
-                            st_cand += (unsigned long long)__popc(smask);
-                            KNN_ITEM_TILE(__popc(smask));
+                if constexpr (MEGA) {
+                    // two cursors walk outwards from u0 (hi up, lo down),
+                    // taking turns; entering a mega-tile, a cursor tests its
+                    // box first and jumps over it when no query can use it
+                    // (thresholds only fall, so a skipped group stays useless)
+                    int hi = u0, lo = u0 - 1, mhi = -1, mlo = -1;
+                    bool up = true;
+                    while (hi < nst || lo >= 0) {
+                        int u;
+                        if (lo < 0 || (up && hi < nst)) {
+                            u = hi;
+                            const int M = u / S2_MEGA;
+                            if (M != mhi) {
+                                mhi = M;
+                                const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
+                                const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
+                                if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
+                                    hi = (M + 1) * S2_MEGA;
+                                    up = false;
+                                    continue;
+                                }
+                            }
+                            ++hi;
                         } else {
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                            u = lo;
+                            const int M = u / S2_MEGA;
+                            if (M != mlo) {
+                                mlo = M;
+                                const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
+                                const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
+                                if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
+                                    lo = M * S2_MEGA - 1;
+                                    up = true;
+                                    continue;
+                                }
+                            }
+                            --lo;
                         }
-                        scan2_tile<DIM, E>(c, s, valid, smask, buf, qc, hist, my_cnt, K, lane);
+                        up = !up;
+                        const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
+                        const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
+                        const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                        if (!smask) continue;
+                        if (DIM >= S2_WIDE_DIM) {
+                            // two tiles per step, as for the flattened runs
+                            for (uint32_t t0 = sb; t0 < se; t0 += 64) {
+                                const bool vA = t0 + lane < se, vB = t0 + 32 + lane < se;
+                                const uint32_t sA = vA ? t0 + lane : 0u, sB = vB ? t0 + 32 + lane : 0u;
+                                float cA[DIM], cB[DIM];
+#pragma unroll
+                                for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
+                                if (vA) load_point<DIM>(a.xsort, sA, cA);
+                                if (vB) load_point<DIM>(a.xsort, sB, cB);
+                                st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
+                                KNN_ITEM_TILE(__popc(smask) * 2);
+                                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane);
+                            }
+                        } else {
+                            scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand);
+                        }
+                    }
+                } else {
+                    // super-tiles alternating outwards from u0, one tile per step
+                    for (int j = 0, left = nst; left > 0; ++j) {
+                        const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
+                        if (u < 0 || u >= nst) continue;
+                        --left;
+                        const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
+                        const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
+                        const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                        if (!smask) continue;
+                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand);
                     }
                 }
             }
