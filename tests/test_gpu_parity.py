@@ -84,6 +84,25 @@ def test_dense_core_in_sparse_background(ctx, d, K):
     assert_same(run(ctx, p, K), oracle.bf(p, K))
 
 
+@pytest.mark.parametrize("d,K", [(2, 64), (4, 32), (6, 16)])
+def test_long_runs_with_outliers(ctx, d, K):
+    # 180k points in a cube of side 1e-4 (cells of the core hold runs of many
+    # 4,096-point mega-tiles), 20k uniform points around it and 300 far
+    # outliers; outlier and background queries sit at coarse levels whose
+    # boxes reach the core, so the mega-tile walk skips most of its runs.
+    # Sampled rows (every outlier, a stride of the rest) against brute force.
+    core = (0.25 + 1e-4 * gen.make_points("uniform", 180000, d, seed=35).astype(np.float64)).astype(np.float32)
+    bg = gen.make_points("uniform", 20000, d, seed=36)
+    far = (4.0 + 3.0 * gen.make_points("uniform", 300, d, seed=37).astype(np.float64)).astype(np.float32)
+    p = np.concatenate([core, bg, far])
+    ids, dist = run(ctx, p, K)
+    rows = np.concatenate([np.arange(0, len(p) - 300, 97), np.arange(len(p) - 300, len(p))])
+    wi, wd = oracle.bf_rows(p, K, rows)
+    bad = np.nonzero((ids[rows] != wi).any(axis=1))[0]
+    assert len(bad) == 0, f"{len(bad)} rows differ, first row {rows[bad[0]]}"
+    np.testing.assert_array_equal(dist[rows], wd)
+
+
 def test_requeued_passes_match(ctx):
     # queries that the first pass cannot certify are re-scanned one level up,
     # starting from the band of the K-th value the first pass found
