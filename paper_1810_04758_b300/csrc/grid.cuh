@@ -429,6 +429,58 @@ __global__ void k_bump_levels(const uint32_t *__restrict__ list, const uint32_t 
     }
 }
 
+// End of a pass, one readback: out[0] = entries of `list` with status 2
+// (buffer overflow), out[1] = entries with status 1 (re-queued), out[2] /
+// out[3] = the smallest / largest level of the status-1 entries, after
+// moving them one level up when `bump` is set (k_bump_levels's rule).
+// out must hold {0, 0, 0xffffffff, 0} on entry (k_summary_init).
+__global__ void k_summary_init(uint32_t *out)
+{
+    if (threadIdx.x == 0) {
+        out[0] = 0u;
+        out[1] = 0u;
+        out[2] = 0xffffffffu;
+        out[3] = 0u;
+    }
+}
+
+__global__ void k_status_summary(const uint32_t *__restrict__ list, const uint32_t *__restrict__ status, int64_t m,
+                                 uint32_t *__restrict__ lvl, uint32_t top, int bump, uint32_t *out)
+{
+    uint32_t c2 = 0, c1 = 0, lmin = 0xffffffffu, lmax = 0;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = list[a];
+        const uint32_t st = status[s];
+        if (st == 2) {
+            ++c2;
+        } else if (st == 1) {
+            ++c1;
+            uint32_t l = lvl[s];
+            if (bump) {
+                l = min(l + 1, top);
+                lvl[s] = l;
+            }
+            lmin = min(lmin, l);
+            lmax = max(lmax, l);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        c2 += __shfl_xor_sync(FULL, c2, o);
+        c1 += __shfl_xor_sync(FULL, c1, o);
+        lmin = min(lmin, __shfl_xor_sync(FULL, lmin, o));
+        lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c2) atomicAdd(&out[0], c2);
+        if (c1) {
+            atomicAdd(&out[1], c1);
+            atomicMin(&out[2], lmin);
+            atomicMax(&out[3], lmax);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a3 / a5
 // ---------------------------------------------------------------------------

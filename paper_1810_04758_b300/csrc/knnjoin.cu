@@ -848,6 +848,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 m = mr;
             }
             row0 = r0;
+            // level range of the next pass, when the last pass's summary gave it
+            bool range_known = false;
+            uint32_t next_lmin = 0, next_lmax = 0;
             while (m > 0) {
                 char pass_name[32];
                 snprintf(pass_name, sizeof(pass_name), "pass %d", pass);
@@ -858,9 +861,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
                 k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
                 k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
-                fetch(pinned, small + 4, 8);
-                CK(cudaStreamSynchronize(s));
-                const uint32_t lmin = pinned[0], lmax = pinned[1];
+                uint32_t lmin = next_lmin, lmax = next_lmax;
+                if (!range_known) {
+                    fetch(pinned, small + 4, 8);
+                    CK(cudaStreamSynchronize(s));
+                    lmin = pinned[0];
+                    lmax = pinned[1];
+                }
+                range_known = false;
                 if (lmax >= (uint32_t)MAX_LEVELS || lmin > lmax) fail(KNN_ERR_CUDA, "internal: level out of range");
                 if (first_level < 0) first_level = (int)lmin;
                 if (lmin != lmax) {
@@ -931,17 +939,38 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                     if (pass < 16) stats.pass_candidates[pass] = (int64_t)c - cand_before;
                     cand_before = (int64_t)c;
                 };
+                // one readback for the end of the pass: overflowed queries,
+                // re-queued queries (moved a level up here under the default
+                // policy) and their level range, which the next pass then
+                // does not read back again
+                bool counts_known = false;
+                int64_t m1 = 0;
                 if (fast) {
-                    // queries whose buffer overflowed (massive ties): general kernel
-                    int64_t mo = select_list(active, m, 2, ovl);
+                    uint32_t *summ = small + 8;
+                    k_summary_init<<<1, 32, 0, s>>>(summ); ++launches;
+                    k_status_summary<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level,
+                                                                          policy == 0 ? 1 : 0, summ); ++launches;
+                    fetch(pinned, summ, 4 * sizeof(uint32_t));
+                    CK(cudaStreamSynchronize(s));
+                    const int64_t mo = pinned[0];
+                    m1 = pinned[1];
+                    next_lmin = pinned[2];
+                    next_lmax = pinned[3];
+                    counts_known = mo == 0;
                     if (mo > 0) {
-                        a.items = make_items(ovl, mo, SCAN_WARPS, nitems);
+                        // queries whose buffer overflowed (massive ties): general kernel
+                        int64_t mo2 = select_list(active, m, 2, ovl);
+                        a.items = make_items(ovl, mo2, SCAN_WARPS, nitems);
                         a.active = ovl;
-                        a.nactive = mo;
+                        a.nactive = mo2;
                         a.nitems = nitems;
                         CK(cudaMemsetAsync(small + 3, 0, 4, s));
                         dispatch_scan(*this, d, a, smem1);
-                        stats.overflow_queries += mo;
+                        stats.overflow_queries += mo2;
+                        // those it could not certify move up a level too
+                        if (policy == 0) {
+                            k_bump_levels<<<grid_for(mo2, 256, nsm), 256, 0, s>>>(ovl, status, mo2, lvl, hp.top_level); ++launches;
+                        }
                     }
                 }
                 if (policy == 1) {
@@ -953,8 +982,22 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                     m = left;
                     break;  // next epoch (or done)
                 }
-                k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
-                int64_t next = select_list(active, m, 1, active2);
+                int64_t next = 0;
+                if (counts_known) {
+                    // the summary counted the re-queued queries: compact without a readback
+                    next = m1;
+                    if (next > 0) {
+                        k_status_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, 1u, flags); ++launches;
+                        scan(flags, rid, m);
+                        k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, flags, rid, m, active2); ++launches;
+                        range_known = true;
+                    }
+                } else {
+                    if (!fast) {
+                        k_bump_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level); ++launches;
+                    }
+                    next = select_list(active, m, 1, active2);
+                }
                 read_pass();
                 if (pass < 16) stats.pass_queries[pass] = m;
                 std::swap(active, active2);
