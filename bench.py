@@ -904,10 +904,10 @@ def run_served(args, rank, world, local_rank):
     nq = sum(len(p) for p in pts)
     torch.cuda.synchronize()
 
-    def serve(workers, rate):
+    def serve(workers, rate, large_first=False):
         """Submit job k at its Poisson arrival time (rate jobs/s; 0 = all at
         once), poll until done; returns (makespan s, latencies ms)."""
-        ctx = kj.Context(device=local_rank, workers=workers)
+        ctx = kj.Context(device=local_rank, workers=workers, large_first=large_first)
         # warm the worker pipelines
         for k in range(min(len(jobs), workers)):
             ctx.self_join(pts[k][:2000].contiguous(), min(Ks[k], 1999))
@@ -946,14 +946,18 @@ def run_served(args, rank, world, local_rank):
         rate = rho * capacity
         span, lat = serve(args.workers or 8, rate)
         span1, lat1 = serve(1, rate)
+        spanp, latp = serve(args.workers or 8, rate, large_first=True)
         lv = sorted(v for v in lat.values() if v is not None)
         lv1 = sorted(v for v in lat1.values() if v is not None)
+        lvp = sorted(v for v in latp.values() if v is not None)
         pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
         results[str(rho)] = {"arrival_jobs_per_s": rate,
                              "p50_ms": pct(lv, 0.5), "p99_ms": pct(lv, 0.99),
                              "q_per_s": nq / span,
                              "fifo_p50_ms": pct(lv1, 0.5), "fifo_p99_ms": pct(lv1, 0.99),
-                             "fifo_q_per_s": nq / span1}
+                             "fifo_q_per_s": nq / span1,
+                             "large_first_p50_ms": pct(lvp, 0.5), "large_first_p99_ms": pct(lvp, 0.99),
+                             "large_first_q_per_s": nq / spanp}
     if rank != 0:
         return 0
     top = results["0.95"]

@@ -86,7 +86,11 @@ typedef struct {
                                  query rows whose device output is at most this many MiB,
                                  each copied out before the next (0 = only when the results
                                  exceed half of the free device memory) */
-    int reserved[5];
+    int large_first;          /* batched/served joins with at least 2^25 output entries (n*K)
+                                 run on high-priority streams, so their blocks are scheduled
+                                 ahead of smaller joins sharing the GPU (shorter tail latency
+                                 for large jobs, a little longer for small ones); 0 = off */
+    int reserved[4];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */

@@ -44,7 +44,7 @@ class KnnjoinConfig(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_jobs", ctypes.c_int),
                 ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
                 ("workers", ctypes.c_int), ("policy", ctypes.c_int), ("out_chunk_mb", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("large_first", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class KnnjoinJob(ctypes.Structure):
@@ -282,7 +282,8 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
                  max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0,
-                 tune_cache_path: Optional[str] = None, policy: int = 0, out_chunk_mb: int = 0):
+                 tune_cache_path: Optional[str] = None, policy: int = 0, out_chunk_mb: int = 0,
+                 large_first: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -300,6 +301,7 @@ class Context:
         cfg.workers = workers
         cfg.policy = policy
         cfg.out_chunk_mb = out_chunk_mb
+        cfg.large_first = 1 if large_first else 0
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None
         cfg.tune_cache_path = self._tune_path
         self._cfg = cfg

@@ -293,6 +293,15 @@ struct Pipeline {
             if (e) cudaEventDestroy(e);
     }
 
+    // run later joins on stream t (waits for this pipeline's work so far)
+    void set_stream(cudaStream_t t)
+    {
+        if (t == s) return;
+        CK(cudaStreamSynchronize(s));
+        s = t;
+        sc.stream = t;
+    }
+
     // copy `bytes` (a multiple of 4) from device memory to host_dst, a
     // position in `pinned`; complete once the stream is synchronised
     void fetch(uint32_t *host_dst, const void *src, size_t bytes)
@@ -1119,6 +1128,7 @@ struct Job {
 struct Worker {
     Pipeline pipe;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream_hi = nullptr;  // highest priority (knnjoin_config.large_first)
     std::thread th;
 };
 
@@ -1219,6 +1229,13 @@ static void worker_loop(knnjoin_ctx *ctx, Worker *w)
         knnjoin_status st = KNN_OK;
         std::string msg;
         try {
+            // large joins first (optional): their launches go to the worker's
+            // high-priority stream; the previous join on this worker has
+            // finished (run() ends with a stream synchronisation)
+            if (w->stream_hi) {
+                const bool large = j->job.n * (int64_t)j->job.K >= Pipeline::BIG_JOB_ENTRIES;
+                w->pipe.set_stream(large ? w->stream_hi : w->stream);
+            }
             validate(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
             w->pipe.run(j->job.points, j->job.n, j->job.d, j->job.K, j->job.out_ids, j->job.out_dist);
         } catch (const KnnError &e) {
@@ -1256,6 +1273,11 @@ static void start_workers(knnjoin_ctx *ctx)
     for (int i = 0; i < ctx->nworkers; ++i) {
         auto w = std::make_unique<Worker>();
         CK(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+        if (ctx->cfg.large_first) {
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(cudaStreamCreateWithPriority(&w->stream_hi, cudaStreamNonBlocking, hi));
+        }
         w->pipe.init(ctx->device, w->stream, &ctx->al);
         w->pipe.big_token = &ctx->big_token;
         w->pipe.width_mult = ctx->main.width_mult;
@@ -1391,9 +1413,11 @@ void knnjoin_destroy(knnjoin_ctx *ctx)
     }
     for (auto &w : ctx->workers) {
         cudaStreamSynchronize(w->stream);
+        if (w->stream_hi) cudaStreamSynchronize(w->stream_hi);
         w->pipe.release();
-        cudaStreamSynchronize(w->stream);
+        cudaStreamSynchronize(w->pipe.s);
         cudaStreamDestroy(w->stream);
+        if (w->stream_hi) cudaStreamDestroy(w->stream_hi);
     }
     ctx->main.release();
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);

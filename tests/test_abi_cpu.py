@@ -55,7 +55,8 @@ def test_struct_layouts_match_header(tmp_path):
                  for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                          check=True).stdout.splitlines())
     assert lines["config"] == [ctypes.sizeof(kj.KnnjoinConfig), kj.KnnjoinConfig.width_mult.offset,
-                               kj.KnnjoinConfig.hbm_budget_bytes.offset, kj.KnnjoinConfig.workers.offset]
+                               kj.KnnjoinConfig.hbm_budget_bytes.offset, kj.KnnjoinConfig.workers.offset,
+                               kj.KnnjoinConfig.large_first.offset]
     assert lines["job"] == [ctypes.sizeof(kj.KnnjoinJob), kj.KnnjoinJob.out_dist.offset]
     assert lines["stats"] == [ctypes.sizeof(kj.KnnjoinStats), kj.KnnjoinStats.candidates.offset,
                               kj.KnnjoinStats.ms_index.offset, kj.KnnjoinStats.ms_wall.offset,

@@ -48,15 +48,20 @@ def test_batch_equals_single_and_oracle(kj):
             np.testing.assert_array_equal(dist.cpu().numpy(), wd)
 
 
-def test_served_results_same_alone_and_in_mix(kj):
+@pytest.mark.parametrize("large_first", [False, True])
+def test_served_results_same_alone_and_in_mix(kj, large_first):
     import torch
     jobs = mixed_jobs(30, seed=5)
+    if large_first:
+        # two joins of >= 2^25 output entries, which go to high-priority streams
+        jobs.insert(3, (gen.make_points("uniform", 600000, 3, seed=6), 64))
+        jobs.insert(20, (gen.make_points("expo", 550000, 4, seed=7), 64))
     with kj.Context(0, workers=4) as alone:
         ref = []
         for p, K in jobs:
             ids, dist = alone.self_join(torch.from_numpy(p).cuda(), K)
             ref.append((ids.cpu(), dist.cpu()))
-    with kj.Context(0, workers=8) as ctx:
+    with kj.Context(0, workers=8, large_first=large_first) as ctx:
         pending = []
         for k, (p, K) in enumerate(jobs):
             t = torch.from_numpy(p).cuda() if k % 2 else torch.from_numpy(p)  # device and host inputs
