@@ -449,7 +449,7 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
         if (lane == 0) qc[i * QP + DIM] = tnew;
         __syncwarp();
     }
-    if (acc && KNN_GUARD(c0 + __popc(bal & lanemask_lt()) < B, 4))
+    if (acc && KNN_GUARD(c0 >= 0 && c0 + __popc(bal & lanemask_lt()) < B, 4))
         bi[c0 + __popc(bal & lanemask_lt())] = ((uint64_t)__float_as_uint(d2) << 32) | s;
     if (lane == i) my_cnt = c0 < 0 ? -1 : c0 + nnew;
 }
@@ -563,9 +563,18 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
         // one vote first for d >= 5, where a step usually accepts nothing
         if (DIM < 5 || __any_sync(FULL, accA || accB)) {
             const uint32_t balA = __ballot_sync(FULL, accA);
-            const uint32_t balB = __ballot_sync(FULL, accB);
-            if (balA) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
-            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB, balB, dB, sB, K, ti, lane);
+            uint32_t balB = __ballot_sync(FULL, accB);
+            float tB = ti;
+            if (balA) {
+                scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
+                // the insert may have shrunk the buffer and lowered the
+                // threshold, or marked the query for the general kernel
+                // (threshold -1, count -1): test the second tile again, so
+                // that nothing is appended to a marked query's buffer
+                tB = qc[i * query_row_floats(DIM) + DIM];
+                balB = __ballot_sync(FULL, accB && dB <= tB);
+            }
+            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB && dB <= tB, balB, dB, sB, K, tB, lane);
         }
     }
 }

@@ -84,3 +84,13 @@ def test_invalid_arguments(ctx):
     with pytest.raises(KnnJoinError):
         ctx.fp32_mismatch(p, bad, [7])
     assert counts(ctx.fp32_mismatch(p, ids, [3, 8])) == oracle.fp32_mismatch(p.cpu().numpy(), ids.cpu().numpy(), [3, 8])
+
+
+@pytest.mark.parametrize("K", [1, 256])
+def test_counts_match_oracle_at_k_extremes(ctx, K):
+    import torch
+    p = gen.make_points("uniform", 6000, 3, seed=95)
+    t = torch.from_numpy(p).cuda()
+    ids, _ = ctx.self_join(t, K)
+    rows = np.arange(0, 6000, 5)
+    assert counts(ctx.fp32_mismatch(t, ids, rows)) == oracle.fp32_mismatch(p, ids.cpu().numpy(), rows)

@@ -155,3 +155,22 @@ def test_context_close_frees_live_indexes():
     assert (ids[:, 0].cpu().numpy() == np.arange(10)).all()
     c.close()      # frees the index too
     ix.close()     # no-op after the context is gone
+
+
+@pytest.mark.parametrize("d,K,Kq", [(1, 8, 30), (8, 16, 4), (3, 200, 256)])
+def test_dimensions_and_k_other_than_the_index(ctx, d, K, Kq):
+    # the index's search distance is chosen for K; queries may ask for more
+    # or fewer neighbours (up to 256 and n)
+    p = gen.make_points("uniform", 9000, d, seed=75 + d)
+    q = gen.make_points("uniform", 2000, d, seed=85 + d)
+    with ctx.index(cuda(p), K) as ix:
+        assert_same(ix.query(cuda(q), Kq), oracle.bf_rs(q, p, Kq))
+
+
+def test_index_of_skewed_data_with_outlier_queries(ctx):
+    # exponential data (density skew: the mega-tile walk) queried by points
+    # spread far beyond the data's box
+    p = gen.make_points("expo", 40000, 3, seed=77)
+    q = (4.0 * gen.make_points("uniform", 3000, 3, seed=78).astype(np.float64) - 1.0).astype(np.float32)
+    with ctx.index(cuda(p), 32) as ix:
+        assert_same(ix.query(cuda(q), 32), oracle.bf_rs(q, p, 32))

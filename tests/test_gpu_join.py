@@ -98,3 +98,15 @@ def test_invalid_arguments(ctx):
         ctx.join(q[:0], p, 5)  # no queries
     with pytest.raises(ValueError):
         ctx.join(q, torch.zeros((100, 3), dtype=torch.float32, device="cuda"), 5)
+
+
+def test_far_queries_on_skewed_data(ctx):
+    # queries far outside an exponential data set: every candidate lies at
+    # nearly the same distance, buffers overflow into the general kernel
+    # within a two-tile step, and the second tile must not append to a
+    # buffer the first tile's insert has just handed over
+    p = gen.make_points("expo", 40000, 3, seed=77)
+    q = (4.0 * gen.make_points("uniform", 3000, 3, seed=78).astype(np.float64) - 1.0).astype(np.float32)
+    got = run(ctx, q, p, 32)
+    assert ctx.stats()["overflow_queries"] > 0
+    assert_same(got, oracle.bf_rs(q, p, 32))
