@@ -459,7 +459,10 @@ template <int DIM, int E, bool MEGA>
 void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
 {
     ensure_nb_order(P.device);
-    constexpr int QM = E <= 4 ? 16 : 8;
+    // queries per work item: 16 with the 64-entry buffers of K <= 32 (5 CTAs
+    // per SM, register-bound either way); 8 with larger buffers, whose
+    // shared memory would otherwise hold an SM to 2 CTAs
+    constexpr int QM = E <= 2 ? 16 : 8;
     static bool configured[64] = {};
     int dev = P.device;
     if (!configured[dev & 63]) {
@@ -766,7 +769,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         // fast kernel (scan2.cuh)
         const bool fast = K + 32 <= 256;
         const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
-        const int QM = E2 <= 4 ? 16 : 8;
+        const int QM = E2 <= 2 ? 16 : 8;  // as in launch_scan2
         const size_t smem2 = scan2_smem_bytes(d, QM, E2);
 
         // per-level cell hash maps, built on first use (a resident index
