@@ -467,7 +467,10 @@ def run_ours(args, rank, world, local_rank):
             for _, jid in inflight:
                 wait(jid)
 
-        run_pipelined(2)
+        # warm-up (untimed): enough steps that every worker pipeline of the
+        # pool has run a join and holds its scratch (a first join on a
+        # pipeline grows the memory pool)
+        run_pipelined(max(2, -(-8 // len(names)) + depth))
         torch.cuda.synchronize()
         e2e_steps = max(4, min(args.steps, 8))
         t0 = time.perf_counter()

@@ -250,9 +250,10 @@ struct Pipeline {
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
-    // and host outputs holds this token while its kernels run and releases it
-    // before copying its results to the host, so such joins take turns on the
-    // SMs and one join's copy overlaps the next one's kernels
+    // and host outputs holds this token from its first pass until its kernels
+    // end and releases it before copying its results to the host, so such
+    // joins take turns on the SMs for their scans, and one join's copy (and
+    // the next one's point upload and index build) overlap another's scan
     std::mutex *big_token = nullptr;
     static constexpr int64_t BIG_JOB_ENTRIES = (int64_t)1 << 25;
     // resident index (knnjoin_index_*): res_mode 1 makes run() index the
@@ -525,9 +526,10 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const bool ids_dev = is_device_ptr(ids_in);
     const bool dist_dev = is_device_ptr(dist_in);
     // large joins whose results go to host memory take turns (see big_token)
+    // (taken just before the first pass, so that the copy of the points and
+    // the index build overlap the scan of the join holding the token)
     std::unique_lock<std::mutex> turn;
-    if (big_token && !(ids_dev && dist_dev) && nrows * (int64_t)K >= BIG_JOB_ENTRIES)
-        turn = std::unique_lock<std::mutex>(*big_token);
+    const bool take_turn = big_token && !(ids_dev && dist_dev) && nrows * (int64_t)K >= BIG_JOB_ENTRIES;
     memset(&stats, 0, sizeof(stats));
     launches = 0;
     double ms_scan = 0.0;
@@ -831,6 +833,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             return cntv;
         };
 
+        if (take_turn && !turn.owns_lock()) turn = std::unique_lock<std::mutex>(*big_token);
         for (int64_t r0 = row_b; r0 < row_e; r0 += chunk_rows) {
             const int64_t r1 = std::min(row_e, r0 + chunk_rows);
             k_iota<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, nq); ++launches;
