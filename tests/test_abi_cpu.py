@@ -92,3 +92,37 @@ def test_null_context_is_rejected(lib):
     assert lib.knnjoin_self_join(None, None, 10, 2, 3, None, None) == kj.KNN_ERR_INVALID
     assert lib.knnjoin_poll(None, 1) == kj.KNN_ERR_INVALID
     lib.knnjoin_destroy(None)
+
+
+def test_null_handles_of_the_newer_entry_points(lib):
+    # no context / no index: rejected without touching a GPU
+    out = (ctypes.c_int64 * 3)()
+    rows = (ctypes.c_int64 * 1)(0)
+    assert lib.knnjoin_fp32_mismatch(None, None, 10, 2, 3, None, rows, 1, out) == kj.KNN_ERR_INVALID
+    assert lib.knnjoin_self_join_rows(None, None, 10, 2, 3, 0, 5, None, None) == kj.KNN_ERR_INVALID
+    ix = ctypes.c_void_p()
+    assert lib.knnjoin_index_create(None, None, 10, 2, 3, ctypes.byref(ix)) == kj.KNN_ERR_INVALID
+    assert lib.knnjoin_index_query(None, None, 1, 3, None, None) == kj.KNN_ERR_INVALID
+    assert lib.knnjoin_index_stats(None, None) == kj.KNN_ERR_INVALID
+    lib.knnjoin_index_destroy(None)
+
+
+@pytest.mark.parametrize("n,world,rank", [(5, 0, 0), (5, 2, 2), (5, 2, -1), (3, 4, 0)])
+def test_shard_rows_rejects_bad_arguments(n, world, rank):
+    with pytest.raises(ValueError):
+        kj.shard_rows(n, world, rank)
+
+
+@pytest.mark.parametrize("workload", ["batched", "served", "join", "index"])
+def test_reference_arm_reports_unavailable_workloads(workload):
+    # the CPU oracle is timed on the unif/expo workloads only; the others
+    # print one JSON line saying so and exit 0 (no GPU needed)
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(HEADER).rsplit(os.sep, 1)[0]
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", workload], capture_output=True, text=True, timeout=120, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and "unavailable" in line
