@@ -654,12 +654,37 @@ __global__ void k_status_flags(const uint32_t *__restrict__ list, const uint32_t
 
 // a11: every output distance holds the bit pattern of its canonical squared
 // distance D; replace it by the correctly rounded sqrt(D) (exact.cuh).
+// Streaming pass: with 16-byte aligned data each thread keeps two 16-byte
+// vectors (four values) in flight per iteration, enough to run near HBM
+// bandwidth; otherwise one value at a time.
 __global__ void k_sqrt_rows(double *__restrict__ dist, int64_t count)
 {
     unsigned long long *u = (unsigned long long *)dist;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x)
-        u[i] = sqrt_bits(u[i]);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    if (((uintptr_t)dist & 15) == 0) {
+        ulonglong2 *v = (ulonglong2 *)dist;
+        const int64_t nv = count / 2;
+        int64_t i = tid;
+        for (; i + nth < nv; i += 2 * nth) {
+            ulonglong2 a = v[i], b = v[i + nth];
+            a.x = sqrt_bits(a.x);
+            a.y = sqrt_bits(a.y);
+            b.x = sqrt_bits(b.x);
+            b.y = sqrt_bits(b.y);
+            v[i] = a;
+            v[i + nth] = b;
+        }
+        for (; i < nv; i += nth) {
+            ulonglong2 a = v[i];
+            a.x = sqrt_bits(a.x);
+            a.y = sqrt_bits(a.y);
+            v[i] = a;
+        }
+        if (tid == 0 && (count & 1)) u[count - 1] = sqrt_bits(u[count - 1]);
+    } else {
+        for (int64_t i = tid; i < count; i += nth) u[i] = sqrt_bits(u[i]);
+    }
 }
 
 // The paper's policy (epochs): flag the sorted positions whose query is not

@@ -197,3 +197,20 @@ def test_invalid_arguments(ctx):
     # the context stays usable after a rejected call
     ids, _ = ctx.self_join(p, 5)
     assert ids.shape == (100, 5)
+
+
+@pytest.mark.parametrize("n,K,offset", [(2001, 3, 0), (2001, 3, 1), (3000, 8, 1)])
+def test_distance_outputs_odd_sized_and_unaligned(ctx, n, K, offset):
+    # the square-root pass works on 16-byte vectors when it can: an odd
+    # number of entries leaves a tail, and an output that starts 8 bytes
+    # into an allocation takes the one-value-at-a-time path
+    import torch
+    p = gen.make_points("uniform", n, 3, seed=91)
+    base = torch.empty(n * K + offset, dtype=torch.float64, device="cuda")
+    dist = base[offset:].view(n, K)
+    ids = torch.empty((n, K), dtype=torch.int32, device="cuda")
+    ctx.self_join(torch.from_numpy(p).cuda(), K, ids, dist)
+    torch.cuda.synchronize()
+    want = oracle.bf(p, K)
+    np.testing.assert_array_equal(ids.cpu().numpy(), want[0])
+    np.testing.assert_array_equal(dist.cpu().numpy(), want[1])
