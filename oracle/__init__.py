@@ -33,6 +33,9 @@ MUTANTS = ("DROP_LAST_TERM", "TIE_DESC", "KEEP_SELF", "LOOSE_CERTIFICATE",
            "NO_LOWER_NEIGHBOUR")
 # planted mistakes in the FP32-only ranking (caught by its own pins)
 FP32_MUTANTS = ("FP32_ONE_CHAIN", "FP32_UNFUSED")
+# planted mistakes in the work count and the search-distance selection
+# (caught by tests/test_oracle_schedule.py)
+SCHEDULE_MUTANTS = ("COUNT_LAST_PASS", "COUNT_SELF", "EPS_BIN_OFF_BY_ONE")
 
 
 def _lib_path(mutant: str | None) -> str:
@@ -50,7 +53,7 @@ def build(mutant: str | None = None, force: bool = False) -> str:
            "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard",
            "-o", out + ".tmp", _SRC, "-lm"]
     if mutant:
-        if mutant not in MUTANTS + FP32_MUTANTS:
+        if mutant not in MUTANTS + FP32_MUTANTS + SCHEDULE_MUTANTS:
             raise ValueError(mutant)
         cmd.insert(1, f"-DORACLE_MUTANT_{mutant}")
     subprocess.run(cmd, check=True)
@@ -212,10 +215,10 @@ def grid_rows(points: np.ndarray, K: int, rows, width_mult: float = 1.0, threads
                            eps_min=st.eps_min, width=st.width)
 
 
-def select_epsilon(points: np.ndarray, K: int, threads: int = 0):
+def select_epsilon(points: np.ndarray, K: int, threads: int = 0, mutant: str | None = None):
     """(eps_min, eps_mean) of the paper's Sec. 4.4 procedure as the oracle reads it."""
     p = _prep(points)
     n, d = p.shape
     em = ctypes.c_double(0.0)
-    e = _load().oracle_select_epsilon(_ptr(p), n, d, K, ctypes.byref(em), threads)
+    e = _load(mutant).oracle_select_epsilon(_ptr(p), n, d, K, ctypes.byref(em), threads)
     return float(e), float(em.value)

@@ -344,7 +344,11 @@ double oracle_select_epsilon(const float *pts, int64_t n, int d, int K,
                 if (j == is) continue;
                 double dist = sqrt(canon_d2(pts + is * d, pts + j * d, d));
                 if (dist < eps_mean) {
+#ifdef ORACLE_MUTANT_EPS_BIN_OFF_BY_ONE
+                    int64_t b = (int64_t)(dist / bw) + 1;
+#else
                     int64_t b = (int64_t)(dist / bw);
+#endif
                     if (b >= GRID_NBINS) b = GRID_NBINS - 1;
                     h[b]++;
                 }
@@ -554,7 +558,11 @@ int oracle_grid_rows(const float *pts, int64_t n, int d, int K, double width_mul
                     if (u < 0) continue;
                     for (int64_t s = L.run_start[u]; s < L.run_start[u] + L.run_len[u]; ++s) {
                         int64_t j = L.order[s];
+#ifdef ORACLE_MUTANT_COUNT_SELF
+                        if (j == i) { ++cand_total; continue; }
+#else
                         if (j == i) continue;
+#endif
                         ++cand_total;
                         topk_insert(top, &cnt, K, canon_d2(q, pts + j * d, d), (int32_t)j);
                     }
@@ -594,7 +602,11 @@ int oracle_grid_rows(const float *pts, int64_t n, int d, int K, double width_mul
             st->pass_queries[lvl] = nactive;
             st->pass_candidates[lvl] = cand_total;
         }
+#ifdef ORACLE_MUTANT_COUNT_LAST_PASS
+        st->candidates = cand_total;
+#else
         st->candidates += cand_total;
+#endif
         st->passes = lvl + 1;
         int64_t m = 0;
         for (int64_t a = 0; a < nactive; ++a)
