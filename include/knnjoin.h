@@ -25,7 +25,8 @@
  * Conventions common to all calls:
  *   - Points are row-major float32 [n][d]; ids are int32 [n][K]; distances
  *     are float64 [n][K].  Pointers may be host or device memory (detected
- *     per call); device pointers must belong to the context's device.
+ *     per call); device pointers must belong to the context's device
+ *     (device memory of another GPU is rejected with KNN_ERR_INVALID).
  *   - The caller owns every buffer it passes.  The library never frees or
  *     retains them past the call (blocking calls) or past the poll that
  *     returns a final status (submitted jobs).  The library owns its index
@@ -286,14 +287,16 @@ const char *knnjoin_last_error(knnjoin_ctx *ctx);
  *   stream   : cudaStream_t to run on (NULL = the legacy default stream)
  *   errbuf   : optional buffer of errlen bytes for the error message
  * The results are identical to knnjoin_self_join's.  The call blocks until
- * the join is done.  KNN_ERR_INVALID for sizes beyond the limits or host
- * pointers; KNN_ERR_NOMEM if an unusually spread-out input needs the cell
- * tables of more grid levels than the array holds.  All calls share the one
- * array, which keeps the previous call's
- * contents; calls that overlap on the GPU race, so the caller serialises
- * them.  The first call on a device sets up that device (looks up the
- * array's address, creates timing events): make it before any stream
- * capture. */
+ * the join is done; an error return also waits for any kernels the call
+ * had queued, so on every return the GPU has stopped using the array.
+ * KNN_ERR_INVALID for sizes beyond the limits, host or managed pointers, or
+ * outputs on a GPU other than the points'; KNN_ERR_NOMEM ("fixed scratch
+ * array exhausted") if an unusually spread-out input needs the cell tables
+ * of more grid levels than the array holds.  All calls share the one array,
+ * which keeps the previous call's contents; calls that overlap on the GPU
+ * race, so the caller serialises them.  The first call on a device sets up
+ * that device (looks up the array's address, creates timing events): make
+ * it before any stream capture. */
 knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t n, int d, int K,
                                          int32_t *out_ids, double *out_dist, void *stream,
                                          char *errbuf, size_t errlen);

@@ -80,12 +80,16 @@ struct Allocator {
     // and release are ordered on the pipeline's stream and never synchronise
     // the device, so pipelines of the worker pool do not stall each other)
     cudaMemPool_t pool = nullptr;
+    // message of a NULL from the hook (null: the generic one)
+    const char *nomem_msg = nullptr;
     void *get(size_t bytes, cudaStream_t s)
     {
         void *p = nullptr;
         if (alloc) {
             p = alloc(bytes, user);
-            if (!p) fail(KNN_ERR_NOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+            if (!p)
+                fail(KNN_ERR_NOMEM, nomem_msg ? std::string(nomem_msg)
+                                              : "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
             return p;
         }
         cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
@@ -144,6 +148,26 @@ bool is_device_ptr(const void *p)
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Where a caller's buffer lives for a join on GPU `dev`: false for host
+// memory (pageable or pinned), true for memory that GPU reads and writes as
+// its own (its device memory, or managed memory).  Device memory of another
+// GPU is an argument error: kernels on `dev` would access a peer's memory
+// (a fault without peer access, a stray peer write with it).
+bool device_side(const void *p, int dev, const char *what)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    if (at.device != dev)
+        fail(KNN_ERR_INVALID, std::string(what) + " is device memory of GPU " + std::to_string(at.device) +
+                                  ", not of GPU " + std::to_string(dev) + " that runs the join");
+    return true;
 }
 
 // Named NVTX range for the lifetime of the object (tracing with nsys/ncu;
@@ -522,9 +546,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const int64_t nrows = row_e - row_b;  // output rows (a shard of the queries, or all)
     const bool sharded = nrows < nq;
     CK(cudaSetDevice(device));
-    const bool pts_dev = is_device_ptr(pts_in);
-    const bool ids_dev = is_device_ptr(ids_in);
-    const bool dist_dev = is_device_ptr(dist_in);
+    const bool pts_dev = device_side(pts_in, device, "points");
+    const bool ids_dev = device_side(ids_in, device, "out_ids");
+    const bool dist_dev = device_side(dist_in, device, "out_dist");
     // large joins whose results go to host memory take turns (see big_token)
     // (taken just before the first pass, so that the copy of the points and
     // the index build overlap the scan of the join holding the token)
@@ -546,7 +570,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const float *qry = pts;
     if (!self) {
         qry = qry_in;
-        if (!is_device_ptr(qry_in)) {
+        if (!device_side(qry_in, device, "queries")) {
             float *p = sc.get<float>("qry_in", (size_t)nq * d);
             CK(cudaMemcpyAsync(p, qry_in, sizeof(float) * nq * d, cudaMemcpyHostToDevice, s));
             qry = p;
@@ -1699,13 +1723,13 @@ knnjoin_status knnjoin_fp32_mismatch(knnjoin_ctx *ctx, const float *points, int6
         Pipeline &P = ctx->main;
         CK(cudaSetDevice(P.device));
         const float *pts = points;
-        if (!is_device_ptr(points)) {
+        if (!device_side(points, P.device, "points")) {
             float *p = P.sc.get<float>("diag_pts", (size_t)n * d);
             CK(cudaMemcpyAsync(p, points, sizeof(float) * n * d, cudaMemcpyHostToDevice, P.s));
             pts = p;
         }
         const int32_t *idd = ids;
-        if (!is_device_ptr(ids)) {
+        if (!device_side(ids, P.device, "ids")) {
             int32_t *p = P.sc.get<int32_t>("diag_ids", (size_t)n * K);
             CK(cudaMemcpyAsync(p, ids, sizeof(int32_t) * n * K, cudaMemcpyHostToDevice, P.s));
             idd = p;
@@ -1824,6 +1848,8 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
     knnjoin_status st = KNN_OK;
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
+    cudaStream_t joined_stream = nullptr;
+    bool started = false;  // kernels may have been queued on the caller's stream
     try {
         validate(points, n, d, K, out_ids, out_dist);
         if (n > KNN_NOALLOC_MAX_POINTS)
@@ -1831,6 +1857,8 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
                                       std::to_string(KNN_NOALLOC_MAX_POINTS) + " points");
         if (noalloc_bytes_needed(n, d) > NOALLOC_SCRATCH_BYTES)
             fail(KNN_ERR_INVALID, "problem does not fit the fixed scratch array");
+        // all three buffers: device memory (not host, not managed) of the
+        // GPU that holds the points, which runs the join
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
             cudaGetLastError();
@@ -1838,9 +1866,17 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
         }
         const int dev = at.device;
         if (dev < 0 || dev >= 64) fail(KNN_ERR_INVALID, "device ordinal out of range");
-        if (!is_device_ptr(out_ids) || !is_device_ptr(out_dist))
-            fail(KNN_ERR_INVALID, "out_ids and out_dist must be device memory");
+        const void *outs[2] = {out_ids, out_dist};
+        for (const void *o : outs) {
+            cudaPointerAttributes ao;
+            if (cudaPointerGetAttributes(&ao, o) != cudaSuccess || ao.type != cudaMemoryTypeDevice ||
+                ao.device != dev) {
+                cudaGetLastError();
+                fail(KNN_ERR_INVALID, "out_ids and out_dist must be device memory of the points' GPU");
+            }
+        }
         CK(cudaSetDevice(dev));
+        joined_stream = (cudaStream_t)stream;
         NoallocDevice &D = g_noalloc_dev[dev];
         {
             std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -1858,6 +1894,8 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
         al.alloc = bump_alloc;
         al.free = bump_free;
         al.user = &bump;
+        al.nomem_msg = "fixed scratch array exhausted: this input needs the cell tables of more grid "
+                       "levels than the no-allocation array holds (use knnjoin_self_join)";
         alignas(64) static thread_local uint32_t readback[1024];
         Pipeline P;
         P.device = dev;
@@ -1876,6 +1914,7 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
         P.sc.get<uint2>("items", (size_t)n + 1);
         P.sc.get<uint32_t>("scan_sums0", (size_t)(n + SCAN_TILE - 1) / SCAN_TILE + 2);
         P.sc.get<uint32_t>("scan_sums1", 4);
+        started = true;
         P.run(points, n, d, K, out_ids, out_dist);
     } catch (const KnnError &e) {
         st = e.st;
@@ -1883,6 +1922,13 @@ extern "C" knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t
     } catch (const std::exception &e) {
         st = KNN_ERR_INVALID;
         msg = e.what();
+    }
+    // an error part-way through a join leaves kernels queued on the caller's
+    // stream that still use the shared array: wait for them, so that every
+    // return (success or error) means the GPU has stopped using it
+    if (st != KNN_OK && started) {
+        cudaStreamSynchronize(joined_stream);
+        cudaGetLastError();
     }
     if (prev_dev >= 0) cudaSetDevice(prev_dev);
     if (errbuf && errlen) {
