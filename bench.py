@@ -15,12 +15,15 @@ step; each step is timed with CUDA events on the library's stream and the
 flush is outside the events.
 
 value = query points per second over the whole job (all ranks); e2e is the
-same metric through the C ABI with pinned host buffers (copies timed).  The
-roofline entry is for the scan kernel, the dominant kernel: algorithmic bytes
-= W_ref * 4d (candidate coordinates, no reuse credited) + n*K*12 (ids and
-FP64 distances written) + n*4d (query points), with W_ref the candidate count
-of the reference grid schedule counted by the oracle's grid join; achieved =
-those bytes / the scan kernel's event-timed duration.
+same metric through the C ABI with pinned host buffers (copies timed).
+Roofline, per join: T_roof = max(T_fp32, T_bytes), T_fp32 = W_ref * (3d - 1)
+flops at the FP32 peak (SMs x 128 lanes x 2 flops x max SM clock), T_bytes =
+n*4d (points read) + n*K*12 (ids and FP64 distances written) bytes at the
+measured HBM peak, with W_ref the candidate count of the reference grid
+schedule counted by the oracle's grid join.  The FP32 term binds the step,
+so the contract's roofline entry is for the scan kernel (the dominant
+kernel) as ALU-bound: achieved = the step's W_ref * (3d - 1) flops / the
+event-timed duration of its scan launches.
 
 Before the warm-up each join's cell-width multiplier is autotuned through
 knnjoin_autotune (untimed; --no-autotune keeps the default 1.25); the value
@@ -76,12 +79,24 @@ WORKLOAD_TEXT = {
 
 
 def peaks():
+    """(HBM GB/s, its kind, SM max MHz) from the driver-written measured peaks,
+    else the fallback figures (6.4 TB/s, 2032 MHz)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             j = json.load(f)
-        return float(j["hbm_gbs"]), "measured"
+        return float(j["hbm_gbs"]), "measured", float(j.get("sm_max_mhz") or 2032.0)
     except Exception:
-        return 6400.0, "fallback"
+        return 6400.0, "fallback", 2032.0
+
+
+# FP32 lanes per SM on B300 (4 sub-partitions x 32); one FMA = 2 flops.
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """Nominal FP32 FMA peak from unit counts and clock: SMs x 128 lanes x 2
+    flops x SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def csrc_digest() -> str:
@@ -97,21 +112,22 @@ def csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes (read + write) of the scan launches of one step, from the
-    committed ncu summary of this workload; None when there is none or the
-    CUDA sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"k_scan2_{workload}_2m.md")
+def profiled_traffic(names):
+    """DRAM bytes (read + write) per step of the scan launches of the named
+    joins, from the committed ncu counters (profiles/k_scan2_traffic.json);
+    None when a join has none or the CUDA sources changed since they were
+    taken."""
     try:
-        with open(path) as f:
-            text = f.read()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "k_scan2_traffic.json")) as f:
+            j = json.load(f)
+    except (OSError, ValueError):
         return None
-    m = re.search(r"^traffic-bytes-per-step: (\d+)$", text, re.M)
-    h = re.search(r"^csrc-sha256-prefix: ([0-9a-f]+)$", text, re.M)
-    if not m or not h or h.group(1) != csrc_digest():
+    if j.get("csrc_sha256_prefix") != csrc_digest():
         return None
-    return int(m.group(1))
+    try:
+        return int(sum(j["joins"][nm]["scan_dram_bytes"] for nm in names))
+    except (KeyError, TypeError):
+        return None
 
 
 def tune_cache_keys(path: str) -> set:
@@ -202,40 +218,61 @@ def max_over_ranks(x: float, device, world: int) -> float:
     return float(t.item())
 
 
-def algorithmic_bytes(name: str, n: int, d: int, K: int, wref: dict) -> tuple[float, float]:
-    """(bytes, fp32 flops) of one join at the roofline, from W_ref."""
+def algorithmic_work(name: str, n: int, d: int, K: int, wref: dict) -> tuple[float, float, float]:
+    """(compulsory bytes, FP32 flops, no-reuse candidate bytes) of one join.
+    Compulsory bytes: the points read once (n*4d) and the ids and FP64
+    distances written once (n*K*12).  Flops: W_ref candidate evaluations x
+    (3d - 1) (d differences, d squares, d - 1 additions), W_ref counted by the
+    oracle's grid schedule.  The candidate bytes W_ref*4d credit no on-chip
+    reuse and are a diagnostic, not a bound."""
     w = wref.get(name, {}).get("candidates")
     if w is None:
-        return float("nan"), float("nan")
-    return float(w) * 4 * d + n * K * 12 + n * 4 * d, float(w) * (3 * d - 1)
+        return float("nan"), float("nan"), float("nan")
+    return float(n * 4 * d + n * K * 12), float(w) * (3 * d - 1), float(w) * 4 * d
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle arm
 # ---------------------------------------------------------------------------
-def oracle_throughput(points_by_name, sample: int, threads: int):
-    """Exact CPU grid join (oracle) throughput, extrapolated to the whole job
-    from a timed sample: T(n) = T_fixed + n * (T(sample) - T_fixed) / sample,
-    where T_fixed is the same call with a single query (search distance and
-    index build over all n points)."""
+def oracle_sample_step(points_by_name, rows: int, threads: int):
+    """One bounded sample of the workload on the CPU oracle (exact grid join,
+    OpenMP on `threads` host cores): for each point set, `rows` strided query
+    rows answered against the whole set -- the search distance and the grid
+    index over all n points are part of every call.  Returns (queries
+    answered, seconds, per-set detail).  Nothing is extrapolated: the rate is
+    queries answered / time spent."""
     import oracle
     total_q, total_t, detail = 0, 0.0, {}
     for name, (p, K) in points_by_name.items():
         n = len(p)
+        r = min(rows, n)
         t0 = time.perf_counter()
-        oracle.grid_rows(p, K, np.array([0]), threads=threads)
-        t_fixed = time.perf_counter() - t0
-        rows = np.linspace(0, n - 1, sample).astype(np.int64)
-        t0 = time.perf_counter()
-        oracle.grid_rows(p, K, rows, threads=threads)
-        t_s = time.perf_counter() - t0
-        per_q = max(t_s - t_fixed, 0.0) / sample
-        t_full = t_fixed + per_q * n
-        total_q += n
-        total_t += t_full
-        detail[name] = {"t_fixed_s": round(t_fixed, 3), "t_sample_s": round(t_s, 3),
-                        "est_full_s": round(t_full, 3)}
-    return total_q / total_t, detail
+        if r >= n:
+            oracle.grid(p, K, threads=threads)
+        else:
+            oracle.grid_rows(p, K, np.linspace(0, n - 1, r).astype(np.int64), threads=threads)
+        dt = time.perf_counter() - t0
+        total_q += r
+        total_t += dt
+        detail[name] = {"rows": r, "s": round(dt, 3)}
+    return total_q, total_t, detail
+
+
+def oracle_full_join(name: str, threads: int):
+    """Seconds of one whole oracle grid join of a named 2M-point set."""
+    import oracle
+    p, K = gen.config_points(name)
+    t0 = time.perf_counter()
+    oracle.grid(p, K, threads=threads)
+    return time.perf_counter() - t0
+
+
+def step_config(args, world: int) -> dict:
+    """The `config` of the unif / expo step (both arms print the same)."""
+    return {"workload": WORKLOAD_TEXT[args.workload], "n": 2_000_000, "d": [2, 4, 6],
+            "K": 64 if args.workload == "expo" else 32,
+            "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def host_cores():
@@ -253,29 +290,30 @@ def run_reference(args, rank, world):
     names = WORKLOADS[args.workload]
     pts = {nm: gen.config_points(nm) for nm in names}
     cores = host_cores()
-    sample = args.cpu_sample
+    rows = args.cpu_sample
     for _ in range(args.warmup):
-        oracle_throughput({names[0]: pts[names[0]]}, max(16, sample // 16), cores)
-    vals = []
-    t0 = time.perf_counter()
+        oracle_sample_step(pts, rows, cores)
+    step_s = []
     detail = {}
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, detail = oracle_throughput(pts, sample, cores)
-        vals.append(v)
+        q, sec, detail = oracle_sample_step(pts, rows, cores)
+        step_s.append(sec)
     wall = time.perf_counter() - t0
-    value = statistics.median(vals)
-    nq = sum(len(p) for p, _ in pts.values())
+    value = q / statistics.median(step_s)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * nq / value,
+        "impl": "reference", "metric": METRIC if args.workload == "unif" else METRIC.replace("K=32", "K=64"),
+        "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(step_s),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n": 2_000_000,
-                   "d": [2, 4, 6], "K": 64 if args.workload == "expo" else 32},
+        "config": step_config(args, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} strided query rows per point set against the full "
-                                   f"2M-point index, extrapolated to all n (index and search "
-                                   f"distance timed separately); median of {args.steps} steps",
+                         "sample": f"per step, {rows} strided query rows of each 2M-point set "
+                                   f"answered by the exact CPU grid join against the whole set "
+                                   f"(search distance and index over all n included); value = "
+                                   f"queries answered / measured step time, median of "
+                                   f"{args.steps} steps, nothing extrapolated",
                          "detail": detail},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(wall, 2),
@@ -377,59 +415,70 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = total_ms / args.steps
     value = world * nq_step / (ms_per_step / 1000.0)
 
-    # roofline of the scan kernel and of the whole join
-    hbm, peak_kind = peaks()
+    # roofline: per join T_roof = max(T_fp32, T_bytes) with T_fp32 = W_ref*(3d-1)
+    # flops at the FP32 peak and T_bytes = compulsory bytes at the HBM peak
+    hbm, peak_kind, sm_max_mhz = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p32 = fp32_peak_tflops(sms, sm_max_mhz)
     wref = wref_table()
-    alg_bytes, alg_flops, roof_ms = 0.0, 0.0, 0.0
+    alg_flops, cand_bytes, roof_ms = 0.0, 0.0, 0.0
     per_summary = {}
     for nm in names:
         p, K = hosts[nm]
         n, d = p.shape
-        b, f = algorithmic_bytes(nm, n, d, K, wref)
-        alg_bytes += b
+        b, f, cb = algorithmic_work(nm, n, d, K, wref)
         alg_flops += f
+        cand_bytes += cb
         st = per_cfg[nm]
         ms_join = statistics.median(s["ms_total"] for s in st)
-        t_roof = b / (hbm * 1e9) * 1e3
+        ms_scan_j = statistics.median(s["ms_scan"] for s in st)
+        t_fp32 = f / (p32 * 1e12) * 1e3
+        t_bytes = b / (hbm * 1e9) * 1e3
+        t_roof = max(t_fp32, t_bytes)
         roof_ms += t_roof
         w_ref = wref.get(nm, {}).get("candidates")
         per_summary[nm] = {
             "ms": round(ms_join, 4), "q_per_s": n / (ms_join / 1e3),
-            "ms_scan": round(statistics.median(s["ms_scan"] for s in st), 4),
+            "ms_scan": round(ms_scan_j, 4),
             "ms_index": round(statistics.median(s["ms_index"] for s in st), 4),
             "passes": st[-1]["passes"], "pass_queries": st[-1]["pass_queries"],
             "ms_pass": [round(x, 3) for x in st[-1]["ms_pass"]],
             "pass_candidates": st[-1]["pass_candidates"],
             "candidates": st[-1]["candidates"], "band_entries": st[-1]["band_entries"],
             "overflow_queries": st[-1]["overflow_queries"],
-            "w_over_wref": (st[-1]["candidates"] / w_ref) if w_ref else None,
-            "t_roof_ms": round(t_roof, 4), "join_roofline_frac": t_roof / ms_join,
+            "w_ref": w_ref, "w_over_wref": (st[-1]["candidates"] / w_ref) if w_ref else None,
+            "t_fp32_ms": round(t_fp32, 4), "t_bytes_ms": round(t_bytes, 4), "t_roof_ms": round(t_roof, 4),
+            "bound": "alu" if t_fp32 >= t_bytes else "hbm",
+            "join_roofline_frac": t_roof / ms_join, "scan_roofline_frac": t_roof / ms_scan_j,
             "fixed_point": st[-1]["fixed_point"], "cell_width": st[-1]["cell_width"],
             "width_mult": st[-1]["width_mult"], "autotuned": nm in tuned,
         }
     scan_ms_per_step = scan_ms / args.steps
-    achieved = alg_bytes / (scan_ms_per_step / 1e3) / 1e9 if scan_ms_per_step > 0 else float("nan")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None if args.configs else profiled_traffic(args.workload),
+    achieved = alg_flops / (scan_ms_per_step / 1e3) / 1e12 if scan_ms_per_step > 0 else float("nan")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s",
+                "frac": achieved / p32,
+                "traffic": None if args.configs else profiled_traffic(names),
                 "kernel": "k_scan2",
-                "peak_kind": peak_kind,
-                "algorithmic_bytes_per_step": alg_bytes,
+                "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
+                             f"{sm_max_mhz:.0f} MHz (max SM clock)",
+                "algorithmic_flops_per_step": alg_flops,
                 "scan_ms_per_step": scan_ms_per_step,
-                "join_frac": roof_ms / ms_per_step,
-                "fp32_only_frac": (alg_flops / 69.2e12 * 1e3) / ms_per_step,
-                "fp32_view": {"bound": "alu", "achieved": alg_flops / (scan_ms_per_step / 1e3) / 1e12
-                              if scan_ms_per_step > 0 else None, "peak": 69.2, "unit": "TFLOP/s",
-                              "frac": (alg_flops / (scan_ms_per_step / 1e3) / 1e12) / 69.2
-                              if scan_ms_per_step > 0 else None,
-                              "what": "W_ref*(3d-1) FP32 flops of the step / the scan launches' event time, "
-                                      "against the measured FFMA peak (profiles/alu_peaks_b300.md); the "
-                                      "kernel is issue-bound (ncu: 57-62% issue active, DRAM 1.5-4% of peak, "
-                                      "profiles/k_scan2_unif_2m.md)"},
-                "note": "frac = scan-kernel achieved / measured HBM copy peak; algorithmic bytes "
-                        "credit no on-chip reuse (W_ref*4d), so frac > 1 where a candidate row "
-                        "serves several queries of an item; traffic = ncu DRAM bytes of the "
-                        "step's pass-1 scan launches (per step, like achieved); join_frac = "
-                        "sum of per-join T_roof / whole-step device time"}
+                "step_frac": roof_ms / ms_per_step,
+                "step_roof_ms": roof_ms,
+                "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind,
+                "note": "achieved = W_ref*(3d-1) FP32 flops of the step's joins / the event-timed "
+                        "duration of the step's scan launches (the FP32 term binds the step: "
+                        "per-join bounds in per_config); step_frac = sum over joins of "
+                        "max(T_fp32, T_bytes) / the whole step's device time, T_bytes = "
+                        "(n*4d + n*K*12) bytes at the HBM peak; traffic = ncu DRAM bytes of "
+                        "the step's scan launches",
+                "diagnostic_candidate_bytes": {
+                    "bytes_per_step": cand_bytes,
+                    "GBps_over_scan": cand_bytes / (scan_ms_per_step / 1e3) / 1e9 if scan_ms_per_step > 0
+                    else None,
+                    "what": "W_ref*4d candidate coordinate bytes with no on-chip reuse credited; a "
+                            "candidate row serves several queries of a work item and the 2M-point "
+                            "set stays in L2, so this is not a bound"}}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -529,12 +578,18 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        v, detail = oracle_throughput(hosts, args.cpu_sample, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_sample} strided query rows per point set against the full "
-                         f"2M-point index (exact CPU grid join, OpenMP), extrapolated to all n "
-                         f"with index and search distance timed separately",
-               "detail": detail}
+        q, sec, detail = oracle_sample_step(hosts, args.cpu_sample, cores)
+        full_name = names[0]
+        full_s = oracle_full_join(full_name, cores)
+        cpu = {"value": q / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} strided query rows of each 2M-point set answered by "
+                         f"the exact CPU grid join (OpenMP) against the whole set, search distance "
+                         f"and index over all n included; value = queries answered / measured "
+                         f"time, nothing extrapolated",
+               "detail": detail,
+               "full_join": {"set": full_name, "rows": len(hosts[full_name][0]), "s": round(full_s, 3),
+                             "q_per_s": len(hosts[full_name][0]) / full_s,
+                             "what": "one whole oracle join of this set, all rows, measured"}}
 
     ctx.close()
     if rank != 0:
@@ -546,9 +601,7 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (scan) + exact canonical-f64 re-score (integer emulation)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n": 2_000_000, "d": [2, 4, 6],
-                   "K": hosts[names[0]][1], "l2": "flushed (256 MiB write) before every timed step",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": step_config(args, world),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -999,7 +1052,8 @@ def main():
     ap.add_argument("--workers", type=int, default=0, help="batched/served: worker pipelines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--cpu-sample", type=int, default=50000,
+                    help="CPU oracle: query rows per point set in one bounded sample")
     ap.add_argument("--fp32-rows", type=int, default=65536,
                     help="sampled rows per point set for the FP32-only mismatch rate (0: skip)")
     ap.add_argument("--policy", type=int, choices=[0, 1], default=0,

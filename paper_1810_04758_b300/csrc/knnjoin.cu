@@ -1347,13 +1347,16 @@ static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f, st
 }
 
 #ifdef KNN_PHASE_TIMING
-// Diagnostics build only: read (and optionally clear) the phase counters.
+// Diagnostic builds only: read (and optionally clear) out[0..16) phase cycles and item figures,
+// out[16..32) event counts of the scan kernel (scan2_debug.cuh).
 extern "C" int knnjoin_debug_phases(unsigned long long *out, int reset)
 {
     if (cudaMemcpyFromSymbol(out, knn::g_phase, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(out + 16, knn::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
     if (reset) {
         unsigned long long z[16] = {};
         if (cudaMemcpyToSymbol(knn::g_phase, z, sizeof(z)) != cudaSuccess) return 1;
+        if (cudaMemcpyToSymbol(knn::g_count, z, sizeof(z)) != cudaSuccess) return 1;
     }
     return 0;
 }

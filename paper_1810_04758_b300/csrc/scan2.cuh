@@ -38,63 +38,11 @@
 #include "common.cuh"
 #include "grid.cuh"
 #include "scan.cuh"
+// diagnostic phase timing and event counts (compiled away unless built with
+// -DKNN_PHASE_TIMING): the KNN_PT / KNN_CNT / KNN_ITEM markers below
+#include "scan2_debug.cuh"
 
 namespace knn {
-
-// Phase timing (diagnostics): built with -DKNN_PHASE_TIMING, lane 0 of every
-// warp adds clock64() deltas per phase of k_scan2 to g_phase; otherwise the
-// markers compile to nothing.
-#ifdef KNN_PHASE_TIMING
-// [0, 8) cycles per phase; per item: [8] max cycles, [9] sum, [10] count,
-// [11] max query-tiles, [12] sum of Q, [13] max cycles / [14] sum / [15]
-// count of items with Q <= 2
-__device__ unsigned long long g_phase[16];
-#define KNN_PT_DECL unsigned long long ph_[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pt_ = clock64()
-#define KNN_PT(i)                                          \
-    do {                                                   \
-        unsigned long long t_ = clock64();                 \
-        ph_[i] += t_ - pt_;                                \
-        pt_ = t_;                                          \
-    } while (0)
-#define KNN_PT_FLUSH                                       \
-    do {                                                   \
-        if ((threadIdx.x & 31) == 0)                       \
-            for (int q_ = 0; q_ < 8; ++q_) atomicAdd(&g_phase[q_], ph_[q_]); \
-    } while (0)
-#define KNN_ITEM_BEGIN unsigned long long it0_ = clock64(), itq_ = 0
-#define KNN_ITEM_TILE(x) itq_ += (x)
-#define KNN_ITEM_END(Q)                                                    \
-    do {                                                                   \
-        if ((threadIdx.x & 31) == 0) {                                     \
-            const unsigned long long dt_ = clock64() - it0_;               \
-            atomicMax(&g_phase[8], dt_);                                   \
-            atomicAdd(&g_phase[9], dt_);                                   \
-            atomicAdd(&g_phase[10], 1ull);                                 \
-            atomicMax(&g_phase[11], itq_);                                 \
-            atomicAdd(&g_phase[12], (unsigned long long)(Q));              \
-            if ((Q) <= 2) {                                                \
-                atomicMax(&g_phase[13], dt_);                              \
-                atomicAdd(&g_phase[14], dt_);                              \
-                atomicAdd(&g_phase[15], 1ull);                             \
-            }                                                              \
-        }                                                                  \
-    } while (0)
-#else
-#define KNN_PT_DECL
-#define KNN_PT(i) \
-    do {          \
-    } while (0)
-#define KNN_PT_FLUSH \
-    do {             \
-    } while (0)
-#define KNN_ITEM_BEGIN
-#define KNN_ITEM_TILE(x) \
-    do {                 \
-    } while (0)
-#define KNN_ITEM_END(Q) \
-    do {                \
-    } while (0)
-#endif
 
 constexpr int S2_WARPS = 4;
 
@@ -424,14 +372,16 @@ __device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, uint32_t
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int i,
                                              bool acc, uint32_t bal, float d2, uint32_t s, int K, float ti,
-                                             int lane)
+                                             int lane KNN_CNT_PARAM)
 {
+    KNN_CNT(9, 1);
     constexpr int B = 32 * E;
     constexpr int QP = query_row_floats(DIM);
     uint64_t *bi = buf + i * B;
     int c0 = __shfl_sync(FULL, my_cnt, i);
     int nnew = __popc(bal);
     if (c0 + nnew > B) {
+        KNN_CNT(10, 1);
         // buffer full: drop to the K-th value's band (rare)
         int2 r2 = shrink_buffer(bi, c0, K, hist, lane, ti);
         c0 = r2.x;
@@ -501,7 +451,8 @@ __device__ __forceinline__ uint32_t super_tile_mask(const ScanArgs &a, uint32_t 
 // against the queries in `tmask` and append the accepted ones to their buffers.
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bool valid, uint32_t tmask,
-                                           uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K, int lane)
+                                           uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K, int lane
+                                           KNN_CNT_PARAM)
 {
     // the queries this tile can serve; for d >= S2_PAIR_DIM, two at a time
     // (independent dependency chains: a query's threshold only
@@ -523,8 +474,8 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
             const bool acc1 = two && valid && d1 <= t1v && s != s1;
             const uint32_t bal0 = __ballot_sync(FULL, acc0);
             const uint32_t bal1 = __ballot_sync(FULL, acc1);
-            if (bal0) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i0, acc0, bal0, d0, s, K, t0v, lane);
-            if (bal1) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i1, acc1, bal1, d1, s, K, t1v, lane);
+            if (bal0) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i0, acc0, bal0, d0, s, K, t0v, lane KNN_CNT_ARG);
+            if (bal1) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i1, acc1, bal1, d1, s, K, t1v, lane KNN_CNT_ARG);
         }
     } else {
         for (uint32_t m = tmask; m; m &= m - 1) {
@@ -535,7 +486,7 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
             const float d2 = dist2_f32<DIM>(qv, c);
             const bool acc = valid && d2 <= ti && s != qi_s;
             const uint32_t bal = __ballot_sync(FULL, acc);
-            if (bal) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, acc, bal, d2, s, K, ti, lane);
+            if (bal) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, acc, bal, d2, s, K, ti, lane KNN_CNT_ARG);
         }
     }
 }
@@ -549,7 +500,7 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const float (&cB)[DIM], uint32_t sA,
                                                 uint32_t sB, uint32_t tmask, uint64_t *buf, float *qc,
-                                                uint32_t *hist, int &my_cnt, int K, int lane)
+                                                uint32_t *hist, int &my_cnt, int K, int lane KNN_CNT_PARAM)
 {
     for (uint32_t m = tmask; m; m &= m - 1) {
         const int i = __ffs(m) - 1;
@@ -562,11 +513,12 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
         const bool accB = dB <= ti && sB != qi_s;
         // one vote first for d >= 5, where a step usually accepts nothing
         if (DIM < 5 || __any_sync(FULL, accA || accB)) {
+            KNN_CNT(11, 1);
             const uint32_t balA = __ballot_sync(FULL, accA);
             uint32_t balB = __ballot_sync(FULL, accB);
             float tB = ti;
             if (balA) {
-                scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane);
+                scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane KNN_CNT_ARG);
                 // the insert may have shrunk the buffer and lowered the
                 // threshold, or marked the query for the general kernel
                 // (threshold -1, count -1): test the second tile again, so
@@ -574,7 +526,7 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
                 tB = qc[i * query_row_floats(DIM) + DIM];
                 balB = __ballot_sync(FULL, accB && dB <= tB);
             }
-            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB && dB <= tB, balB, dB, sB, K, tB, lane);
+            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB && dB <= tB, balB, dB, sB, K, tB, lane KNN_CNT_ARG);
         }
     }
 }
@@ -583,7 +535,7 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_super_tile(const ScanArgs &a, uint32_t sb, uint32_t se, uint32_t smask,
                                                  uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int K,
-                                                 int lane, unsigned long long &st_cand)
+                                                 int lane, unsigned long long &st_cand KNN_CNT_PARAM)
 {
     for (uint32_t t0 = sb; t0 < se; t0 += 32) {
         const bool valid = t0 + lane < se;
@@ -596,7 +548,7 @@ __device__ __forceinline__ void scan2_super_tile(const ScanArgs &a, uint32_t sb,
 #pragma unroll
             for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
         }
-        scan2_tile<DIM, E>(c, s, valid, smask, buf, qc, hist, my_cnt, K, lane);
+        scan2_tile<DIM, E>(c, s, valid, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
     }
 }
 
@@ -762,6 +714,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     if (!(lb > qc[i * QP + DIM] * (1.0f + 0x1p-19f))) cmask |= 1u << i;
                 }
             }
+            KNN_CNT(3, __popc(__ballot_sync(FULL, len != 0)));
+            KNN_CNT(4, __popc(__ballot_sync(FULL, cmask != 0)));
             // long runs first, outside the flattened scan
             const bool bigcell = len >= S2_BIG;
             const uint32_t bigmask = __ballot_sync(FULL, bigcell && cmask != 0);
@@ -817,7 +771,9 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                         const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
                         const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
                         const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                        KNN_CNT(7, 1);
                         if (!smask) continue;
+                        KNN_CNT(6, 1);
                         if (DIM >= S2_WIDE_DIM) {
                             // two tiles per step, as for the flattened runs
                             for (uint32_t t0 = sb; t0 < se; t0 += 64) {
@@ -830,10 +786,10 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                                 if (vB) load_point<DIM>(a.xsort, sB, cB);
                                 st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
                                 KNN_ITEM_TILE(__popc(smask) * 2);
-                                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane);
+                                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
                             }
                         } else {
-                            scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand);
+                            scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
                         }
                     }
                 } else {
@@ -846,7 +802,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                         const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
                         const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
                         if (!smask) continue;
-                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand);
+                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
                     }
                 }
             }
@@ -859,6 +815,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             }
             const uint32_t exc = inc - flen;
             const uint32_t total = __shfl_sync(FULL, inc, 31);
+            KNN_CNT(5, total);
             KNN_PT(1);
             // flattened position t -> (sorted position, cell's query mask)
             auto locate = [&](uint32_t t, bool valid, uint32_t &sp, uint32_t &cmo) {
@@ -881,6 +838,9 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     locate(t0 + lane, vA, sA, cmA);
                     locate(t0 + 32 + lane, vB, sB, cmB);
                     const uint32_t tmask = __reduce_or_sync(FULL, cmA | cmB);
+                    KNN_CNT(0, 1);
+                    KNN_CNT(1, __popc(tmask));
+                    KNN_CNT(2, tmask == 0);
                     // lanes past the end get NaN coordinates: every distance
                     // comparison with them is false
                     float cA[DIM], cB[DIM];
@@ -890,7 +850,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     if (vB && KNN_GUARD(sB < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sB, cB);
                     st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
                     KNN_ITEM_TILE(__popc(tmask) * 2);
-                    scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane);
+                    scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
                 }
             } else {
                 for (uint32_t t0 = 0; t0 < total; t0 += 32) {
@@ -907,7 +867,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
 #pragma unroll
                         for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
                     }
-                    scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane);
+                    scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
                 }
             }
             KNN_PT(2);
@@ -986,6 +946,8 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     }
                 }
                 if (lane == 0) st_band += (unsigned long long)m;
+                KNN_CNT(12, c0);
+                KNN_CNT(13, m);
                 KNN_PT(5);
                 // the FP32 order is the exact order unless two near-equal
                 // values swap; check neighbours, re-sort by (D, id) if needed
@@ -996,7 +958,10 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 const uint64_t nd = __shfl_down_sync(FULL, D[0], 1);
                 const uint32_t ni = __shfl_down_sync(FULL, I[0], 1);
                 inv = inv || (lane < 31 && (lane + 1) * E < m && xless(nd, ni, D[E - 1], I[E - 1]));
-                if (__any_sync(FULL, inv)) warp_bitonic<E>(D, I, lane);
+                if (__any_sync(FULL, inv)) {
+                    KNN_CNT(14, 1);
+                    warp_bitonic<E>(D, I, lane);
+                }
                 uint64_t dk = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e)
