@@ -140,4 +140,51 @@ __device__ __forceinline__ uint64_t f32_to_f64_bits_floor(float f)
     return ((uint64_t)(e8 - 127 + 1023) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
 }
 
+// Hash map (open addressing, linear probing) from level cell key to its run
+// [begin, end) in key order.  One 16-byte slot per entry -- key (x, y),
+// begin (z), end (w) -- so a probe is a single vector load.  Capacity is a
+// power of two >= 2 x cells.  Built by k_hash_insert (grid.cuh).
+constexpr uint64_t HASH_EMPTY = ~0ull;
+
+__device__ __forceinline__ uint2 hash_lookup(const uint4 *__restrict__ slot, uint32_t hmask, uint64_t P)
+{
+    uint32_t h = (uint32_t)mix64(P) & hmask;
+    for (uint32_t probe = 0; probe <= hmask; ++probe) {
+        const uint4 v = __ldg(&slot[h]);
+        const uint64_t k = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        if (k == P) return make_uint2(v.z, v.w);
+        if (k == HASH_EMPTY) break;
+        h = (h + 1) & hmask;
+    }
+    return make_uint2(0, 0);
+}
+
+// Block-wide exclusive scan of one value per thread; `sm` holds >= 32 words.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total, uint32_t *sm)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sm[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        sm[lane] = w;
+    }
+    __syncthreads();
+    uint32_t off = warp ? sm[warp - 1] : 0;
+    total = sm[nw - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
 }  // namespace knn

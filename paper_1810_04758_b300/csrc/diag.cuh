@@ -22,7 +22,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
-#include "scan2.cuh"
+#include "dist32.cuh"
 
 namespace knn {
 

@@ -307,6 +307,29 @@ KNN_HD bool canon_d2_fixed(const int32_t *A, const int32_t *B, int F, uint64_t &
     return true;
 }
 
+#ifdef __CUDACC__
+// The same N from FP32 differences, for q and c on the common grid 2^-F:
+// q - c is exact in FP32 whenever |Xq - Xc| < 2^24 (the exact difference is
+// then representable), and (q - c) * 2^F (sc = 2^F) is that integer exactly.
+// A rounded difference has |x| >= 2^24, which the test catches: false, and
+// the caller takes the integer path above.
+template <int DIM>
+__device__ __forceinline__ bool canon_d2_fixed_f32(const float (&q)[DIM], const float (&c)[DIM], float sc, int F,
+                                                   uint64_t &bits)
+{
+    uint64_t N = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float x = __fmul_rn(__fsub_rn(q[k], c[k]), sc);
+        if (!(fabsf(x) < 16777216.0f)) return false;
+        const int64_t X = (int64_t)__float2int_rz(x);
+        N += (uint64_t)(X * X);
+    }
+    bits = encode_int(N, -2 * F);  // N < 8 * 2^48 < 2^53: exact
+    return true;
+}
+#endif
+
 KNN_HD bool canon_d2_fixed_rt(const int32_t *A, const int32_t *B, int d, int F, uint64_t &bits)
 {
     uint64_t N = 0;

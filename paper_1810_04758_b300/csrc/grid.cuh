@@ -540,12 +540,7 @@ __global__ void k_run_begin(const uint32_t *__restrict__ flags, const uint32_t *
     }
 }
 
-// Hash map (open addressing, linear probing) from level cell key to its run
-// [begin, end) in key order.  One 16-byte slot per entry -- key (x, y),
-// begin (z), end (w) -- so a probe is a single vector load.  Capacity is a
-// power of two >= 2 x cells.
-constexpr uint64_t HASH_EMPTY = ~0ull;
-
+// Insertion into the level hash map (common.cuh: layout and lookup).
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
                               const uint32_t *ncells_p, int shift, uint4 *slot, uint32_t hmask)
 {
@@ -563,19 +558,6 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t 
             h = (h + 1) & hmask;
         }
     }
-}
-
-__device__ __forceinline__ uint2 hash_lookup(const uint4 *__restrict__ slot, uint32_t hmask, uint64_t P)
-{
-    uint32_t h = (uint32_t)mix64(P) & hmask;
-    for (uint32_t probe = 0; probe <= hmask; ++probe) {
-        const uint4 v = __ldg(&slot[h]);
-        const uint64_t k = (uint64_t)v.x | ((uint64_t)v.y << 32);
-        if (k == P) return make_uint2(v.z, v.w);
-        if (k == HASH_EMPTY) break;
-        h = (h + 1) & hmask;
-    }
-    return make_uint2(0, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -41,7 +41,7 @@
 #include "grid.cuh"
 #include "primitives.cuh"
 #include "scan.cuh"
-#include "scan2.cuh"
+#include "scan2_launch.h"
 #include "diag.cuh"
 
 using namespace knn;
@@ -452,88 +452,44 @@ size_t scan2_smem_bytes(int d, int QM, int E)
     return (size_t)S2_WARPS * scan2_warp_bytes(d, QM, E);
 }
 
-// Fill the nearest-first neighbour order (scan2.cuh) on the current device.
-void ensure_nb_order(int dev)
-{
-    static std::mutex mu;
-    static bool done[64] = {};
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[dev & 63]) return;
-    std::vector<uint16_t> tab;
-    tab.reserve(NB_ORDER_TOTAL);
-    for (int d = 1; d <= MAX_DIM; ++d) {
-        int no = 1;
-        for (int k = 0; k < d; ++k) no *= 3;
-        std::vector<std::pair<int, int>> v;
-        for (int o = 0; o < no; ++o) {
-            int moves = 0, r = o;
-            for (int k = 0; k < d; ++k) {
-                moves += (r % 3) != 1;
-                r /= 3;
-            }
-            v.push_back({moves, o});
-        }
-        std::stable_sort(v.begin(), v.end());
-        for (auto &e : v) tab.push_back((uint16_t)e.second);
-    }
-    CK(cudaMemcpyToSymbol(g_nb_order, tab.data(), tab.size() * sizeof(uint16_t)));
-    done[dev & 63] = true;
-}
-
-template <int DIM, int E, bool MEGA>
-void launch_scan2(Pipeline &P, const ScanArgs &a, size_t smem)
-{
-    ensure_nb_order(P.device);
-    // queries per work item: 16 with the 64-entry buffers of K <= 32 (5 CTAs
-    // per SM, register-bound either way); 8 with larger buffers, whose
-    // shared memory would otherwise hold an SM to 2 CTAs
-    constexpr int QM = E <= 2 ? 16 : 8;
-    static bool configured[64] = {};
-    int dev = P.device;
-    if (!configured[dev & 63]) {
-        CK(cudaFuncSetAttribute(k_scan2<DIM, QM, E, MEGA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        configured[dev & 63] = true;
-    }
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan2<DIM, QM, E, MEGA>, S2_CTA, smem));
-    if (occ < 1) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
-    unsigned grid = (unsigned)std::min<int64_t>(((int64_t)a.nitems + S2_WARPS - 1) / S2_WARPS,
-                                                (int64_t)occ * P.nsm);
-    if (grid == 0) return;
-    k_scan2<DIM, QM, E, MEGA><<<grid, S2_CTA, smem, P.s>>>(a);
-    ++P.launches;
-    CK(cudaGetLastError());
-}
-
-template <int DIM>
-void dispatch_scan2_e(Pipeline &P, int E, bool mega, const ScanArgs &a, size_t smem)
-{
-    switch (E * 2 + (mega ? 1 : 0)) {
-    case 4: launch_scan2<DIM, 2, false>(P, a, smem); break;
-    case 5: launch_scan2<DIM, 2, true>(P, a, smem); break;
-    case 8: launch_scan2<DIM, 4, false>(P, a, smem); break;
-    case 9: launch_scan2<DIM, 4, true>(P, a, smem); break;
-    case 16: launch_scan2<DIM, 8, false>(P, a, smem); break;
-    case 17: launch_scan2<DIM, 8, true>(P, a, smem); break;
-    default: fail(KNN_ERR_INVALID, "internal: bad buffer size");
-    }
-}
-
-// mega: the long-run walk that skips mega-tiles (k_scan2's MEGA)
+// The scan kernel k_scan2 for dimension d (its instances live in one
+// translation unit per d, scan2_launch.cu); mega: the long-run walk that
+// skips mega-tiles.
 void dispatch_scan2(Pipeline &P, int d, int E, bool mega, const ScanArgs &a, size_t smem)
 {
+    bool nofit = false;
+    cudaError_t e;
     switch (d) {
-    case 1: dispatch_scan2_e<1>(P, E, mega, a, smem); break;
-    case 2: dispatch_scan2_e<2>(P, E, mega, a, smem); break;
-    case 3: dispatch_scan2_e<3>(P, E, mega, a, smem); break;
-    case 4: dispatch_scan2_e<4>(P, E, mega, a, smem); break;
-    case 5: dispatch_scan2_e<5>(P, E, mega, a, smem); break;
-    case 6: dispatch_scan2_e<6>(P, E, mega, a, smem); break;
-    case 7: dispatch_scan2_e<7>(P, E, mega, a, smem); break;
-    case 8: dispatch_scan2_e<8>(P, E, mega, a, smem); break;
+    case 1: e = scan2_launch<1>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 2: e = scan2_launch<2>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 3: e = scan2_launch<3>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 4: e = scan2_launch<4>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 5: e = scan2_launch<5>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 6: e = scan2_launch<6>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 7: e = scan2_launch<7>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 8: e = scan2_launch<8>(a, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
     default: fail(KNN_ERR_INVALID, "d out of range");
     }
+    if (e == cudaErrorInvalidValue) fail(KNN_ERR_INVALID, "internal: bad buffer size");
+    ck(e, "scan kernel launch");
+    if (nofit) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
 }
+
+#ifdef KNN_CHECKS
+// Failed-check words of every kernel unit (checked builds).
+unsigned all_check_words(bool clear)
+{
+    unsigned w = 0, z = 0, h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_check_word, sizeof(h)) == cudaSuccess && h) {
+        w |= h;
+        if (clear) cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));
+    }
+    w |= scan2_check_word<1>(clear) | scan2_check_word<2>(clear) | scan2_check_word<3>(clear) |
+         scan2_check_word<4>(clear) | scan2_check_word<5>(clear) | scan2_check_word<6>(clear) |
+         scan2_check_word<7>(clear) | scan2_check_word<8>(clear);
+    return w;
+}
+#endif
 
 void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
                    const float *qry_in, int64_t nq_in, int64_t row_b, int64_t row_e)
@@ -795,7 +751,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         // fast kernel (scan2.cuh)
         const bool fast = K + 32 <= 256;
         const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
-        const int QM = E2 <= 2 ? 16 : 8;  // as in launch_scan2
+        const int QM = scan2_queries_per_item(E2);
         const size_t smem2 = scan2_smem_bytes(d, QM, E2);
 
         // per-level cell hash maps, built on first use (a resident index
@@ -1075,10 +1031,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     CK(cudaGetLastError());
 #ifdef KNN_CHECKS
     {
-        unsigned w = 0, z = 0;
-        CK(cudaMemcpyFromSymbol(&w, g_check_word, sizeof(w)));
+        const unsigned w = all_check_words(true);
         if (w) {
-            CK(cudaMemcpyToSymbol(g_check_word, &z, sizeof(z)));
             char msg[96];
             snprintf(msg, sizeof(msg), "bounds check failed (sites 0x%x)", w);
             fail(KNN_ERR_CUDA, msg);
@@ -1347,17 +1301,18 @@ static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f, st
 }
 
 #ifdef KNN_PHASE_TIMING
-// Diagnostic builds only: read (and optionally clear) out[0..16) phase cycles and item figures,
-// out[16..32) event counts of the scan kernel (scan2_debug.cuh).
+// Diagnostic builds only: read (and optionally clear) the scan kernel's
+// phase cycles and item figures (out[0..16)) and event counts (out[16..32)),
+// summed over the kernel's units (scan2_debug.cuh).
 extern "C" int knnjoin_debug_phases(unsigned long long *out, int reset)
 {
-    if (cudaMemcpyFromSymbol(out, knn::g_phase, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-    if (cudaMemcpyFromSymbol(out + 16, knn::g_count, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-    if (reset) {
-        unsigned long long z[16] = {};
-        if (cudaMemcpyToSymbol(knn::g_phase, z, sizeof(z)) != cudaSuccess) return 1;
-        if (cudaMemcpyToSymbol(knn::g_count, z, sizeof(z)) != cudaSuccess) return 1;
-    }
+    for (int i = 0; i < 32; ++i) out[i] = 0;
+    const bool r = reset != 0;
+    if (scan2_debug_read<1>(out, r) != cudaSuccess || scan2_debug_read<2>(out, r) != cudaSuccess ||
+        scan2_debug_read<3>(out, r) != cudaSuccess || scan2_debug_read<4>(out, r) != cudaSuccess ||
+        scan2_debug_read<5>(out, r) != cudaSuccess || scan2_debug_read<6>(out, r) != cudaSuccess ||
+        scan2_debug_read<7>(out, r) != cudaSuccess || scan2_debug_read<8>(out, r) != cudaSuccess)
+        return 1;
     return 0;
 }
 #endif

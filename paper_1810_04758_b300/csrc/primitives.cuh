@@ -17,34 +17,6 @@ constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-// Block-wide exclusive scan of one value per thread; `sm` holds >= 32 words.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total, uint32_t *sm)
-{
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sm[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < nw ? sm[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += y;
-        }
-        sm[lane] = w;
-    }
-    __syncthreads();
-    uint32_t off = warp ? sm[warp - 1] : 0;
-    total = sm[nw - 1];
-    __syncthreads();
-    return off + x - v;
-}
-
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t *in, uint32_t *out,
                                                             uint32_t *sums, int64_t n)
 {

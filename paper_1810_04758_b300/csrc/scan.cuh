@@ -28,7 +28,6 @@
 // exact round in which every candidate carries its exact (D, id) key.
 #pragma once
 #include "common.cuh"
-#include "grid.cuh"
 
 namespace knn {
 
@@ -79,7 +78,7 @@ __device__ __forceinline__ float band_thr(uint32_t tbits)
 }
 
 // K-th smallest (1-based k, 1 <= k <= cnt) of non-negative float bit patterns.
-__device__ uint32_t warp_select(const uint32_t *keys, int cnt, int k, uint32_t *hist, int lane)
+static __device__ uint32_t warp_select(const uint32_t *keys, int cnt, int k, uint32_t *hist, int lane)
 {
     uint32_t prefix = 0, mask = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
@@ -128,7 +127,7 @@ __device__ uint32_t warp_select(const uint32_t *keys, int cnt, int k, uint32_t *
 }
 
 // Keep entries with key <= thr (in place, any order); returns the new count.
-__device__ int warp_compact(uint32_t *key, uint32_t *idx, int cnt, uint32_t thr_bits, int lane)
+static __device__ int warp_compact(uint32_t *key, uint32_t *idx, int cnt, uint32_t thr_bits, int lane)
 {
     int out = 0;
     for (int base = 0; base < cnt; base += 32) {

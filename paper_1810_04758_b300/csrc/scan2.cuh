@@ -36,15 +36,15 @@
 //       correctly rounded square roots are taken afterwards, k_sqrt_rows).
 #pragma once
 #include "common.cuh"
-#include "grid.cuh"
 #include "scan.cuh"
+#include "dist32.cuh"
+#include "scan2_launch.h"
 // diagnostic phase timing and event counts (compiled away unless built with
 // -DKNN_PHASE_TIMING): the KNN_PT / KNN_CNT / KNN_ITEM markers below
 #include "scan2_debug.cuh"
 
 namespace knn {
 
-constexpr int S2_WARPS = 4;
 
 // Runs of at least S2_BIG points are scanned in super-tiles of S2_SUPER
 // consecutive points, each skipped by the queries it cannot serve.
@@ -94,7 +94,6 @@ __host__ __device__ constexpr int nb_order_offset(int d)
 {
     return d <= 1 ? 0 : nb_order_offset(d - 1) + (d == 2 ? 3 : d == 3 ? 9 : d == 4 ? 27 : d == 5 ? 81 : d == 6 ? 243 : d == 7 ? 729 : 2187);
 }
-constexpr int S2_CTA = S2_WARPS * 32;
 
 template <int DIM>
 __device__ __forceinline__ void load_point(const float *__restrict__ xs, uint32_t s, float (&c)[DIM])
@@ -120,7 +119,7 @@ __device__ __forceinline__ void load_point(const float *__restrict__ xs, uint32_
 
 // K-th smallest (1 <= k <= cnt) of the high 32 bits (non-negative float bit
 // patterns) of buf[0..cnt).
-__device__ uint32_t warp_select_hi(const uint64_t *buf, int cnt, int k, uint32_t *hist, int lane)
+static __device__ uint32_t warp_select_hi(const uint64_t *buf, int cnt, int k, uint32_t *hist, int lane)
 {
     uint32_t prefix = 0, mask = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
@@ -170,7 +169,7 @@ __device__ uint32_t warp_select_hi(const uint64_t *buf, int cnt, int k, uint32_t
 }
 
 // Keep entries whose high 32 bits are <= thr (in place); returns the count.
-__device__ int warp_compact_hi(uint64_t *buf, int cnt, uint32_t thr, int lane)
+static __device__ int warp_compact_hi(uint64_t *buf, int cnt, uint32_t thr, int lane)
 {
     int out = 0;
     for (int base = 0; base < cnt; base += 32) {
@@ -236,25 +235,6 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&D)[E], uint32_t (&I)[E],
     }
 }
 
-// Row of a query in shared memory: coordinates, current threshold, sorted
-// position (as float bits), padded to a multiple of 4 floats (vector loads).
-__host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) & ~3; }
-
-// Entries of the per-item table of neighbour key parts (even, so that what
-// follows stays 16-byte aligned).
-__host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; }
-
-// Bytes of one warp's shared memory in k_scan2 (16-byte multiple):
-// candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
-// [QM][QP] f32, counts and sorted positions [QM] x 2, radix histogram [256],
-// squared face gaps [QM][3d] f32, the item's cell and the level's extent
-// [2d] i32.
-__host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
-{
-    return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
-            (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)2 * d * 4 + 15) & ~(size_t)15;
-}
-
 template <int DIM>
 __device__ __forceinline__ void load_query_row(const float *qc, int i, float (&q)[DIM], float &thr, uint32_t &qs)
 {
@@ -273,32 +253,6 @@ __device__ __forceinline__ void load_query_row(const float *qc, int i, float (&q
     for (int k = 0; k < DIM; ++k) q[k] = r[k];
     thr = r[DIM];
     qs = __float_as_uint(r[DIM + 1]);
-}
-
-// FP32 squared distance; for d >= 4 even and odd dimensions accumulate in two
-// chains (shorter latency).  Either way the value is within (d + 2) 2^-24
-// relative of the exact squared distance (plus underflow terms far below
-// 2^-120), which the band factor 2^-15 covers.
-template <int DIM>
-__device__ __forceinline__ float dist2_f32(const float (&q)[DIM], const float (&c)[DIM])
-{
-    if (DIM < 4) {
-        float d2 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-            const float df = q[k] - c[k];
-            d2 = fmaf(df, df, d2);
-        }
-        return d2;
-    }
-    float e = 0.0f, o = 0.0f;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        const float df = q[k] - c[k];
-        if (k & 1) o = fmaf(df, df, o);
-        else e = fmaf(df, df, e);
-    }
-    return e + o;
 }
 
 // Bitonic sort, ascending, of 32*E 32-bit values held E per lane in blocked
@@ -352,13 +306,34 @@ __device__ __forceinline__ float cert_radius(const float *q, const int *cell, co
     return a.rcap > 0.0f ? fminf(R, a.rcap) : R;  // the paper's policy: K within eps
 }
 
+// K-th smallest (1 <= k <= cnt <= 32*E) of the high 32 bits of
+// buf[0..cnt), by a warp bitonic sort of the words (E per lane); for small
+// buffers this takes about half the instructions of the radix select.
+template <int E>
+__device__ __forceinline__ uint32_t warp_kth_hi_sort(const uint64_t *buf, int cnt, int k, int lane)
+{
+    uint32_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = lane * E + e;
+        v[e] = g < cnt ? (uint32_t)(buf[g] >> 32) : 0xffffffffu;
+    }
+    warp_bitonic_u32<E>(v, lane);
+    uint32_t r = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e == (k - 1) % E) r = v[e];
+    return __shfl_sync(FULL, r, (k - 1) / E);
+}
+
 // Buffer full: find its K-th value T, lower the threshold to the band of T
 // and keep only the entries within it.  Returns (new count, new threshold
 // bits).  Kept out of line: it runs rarely.
-__device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, uint32_t *hist, int lane, float thr)
+template <int E>
+static __device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, uint32_t *hist, int lane, float thr)
 {
     __syncwarp();
-    uint32_t T = warp_select_hi(bi, c0, K, hist, lane);
+    const uint32_t T = E <= 2 ? warp_kth_hi_sort<E>(bi, c0, K, lane) : warp_select_hi(bi, c0, K, hist, lane);
     float nt = fminf(thr, band_thr(T));
     int c1 = warp_compact_hi(bi, c0, __float_as_uint(nt), lane);
     __syncwarp();
@@ -383,7 +358,7 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
     if (c0 + nnew > B) {
         KNN_CNT(10, 1);
         // buffer full: drop to the K-th value's band (rare)
-        int2 r2 = shrink_buffer(bi, c0, K, hist, lane, ti);
+        int2 r2 = shrink_buffer<E>(bi, c0, K, hist, lane, ti);
         c0 = r2.x;
         const float nt = __int_as_float(r2.y);
         acc = acc && d2 <= nt;
@@ -502,13 +477,17 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
                                                 uint32_t sB, uint32_t tmask, uint64_t *buf, float *qc,
                                                 uint32_t *hist, int &my_cnt, int K, int lane KNN_CNT_PARAM)
 {
+    // the two candidates' coordinates packed per dimension (once per step)
+    unsigned long long cp[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) cp[k] = f32x2_pack(cA[k], cB[k]);
     for (uint32_t m = tmask; m; m &= m - 1) {
         const int i = __ffs(m) - 1;
         float qv[DIM], ti;
         uint32_t qi_s;
         load_query_row<DIM>(qc, i, qv, ti, qi_s);
-        const float dA = dist2_f32<DIM>(qv, cA);
-        const float dB = dist2_f32<DIM>(qv, cB);
+        float dA, dB;
+        dist2_f32_x2<DIM>(qv, cp, dA, dB);
         const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
         const bool accB = dB <= ti && sB != qi_s;
         // one vote first for d >= 5, where a step usually accepts nothing
@@ -581,9 +560,13 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
     // query to the lower neighbour cell, 0 (same slab), to the upper one --
     // indexed by the base-3 digit of a neighbour offset
     float *gsq = (float *)(hist + 256);
-    int *cellv = (int *)(gsq + QM * GQ);       // [2d]
+    float *rcert = gsq + QM * GQ;              // [QM] certificate radius of each query
+    int *cellv = (int *)(rcert + QM);          // [2d]
 
     unsigned long long st_cand = 0, st_band = 0;
+    // 2^F as a float for the fixed-point distance from FP32 differences (0:
+    // F outside the normal exponent range, that path unused)
+    const float fsc = (a.fixed_ok && a.F >= -126 && a.F <= 127) ? __int_as_float((a.F + 127) << 23) : 0.0f;
     KNN_PT_DECL;
 
     for (;;) {
@@ -666,6 +649,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             // of the K-th value an earlier pass found in a smaller box
             // (contained in this one), whichever is lower
             const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
+            rcert[lane] = R;
             const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
                                    ? __int_as_float(0x7f800000)
                                    : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
@@ -806,7 +790,9 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     }
                 }
             }
-            const uint32_t flen = bigcell ? 0u : len;
+            // (cells that no query of the item can use stay out of the
+            // flattened list)
+            const uint32_t flen = (bigcell || cmask == 0) ? 0u : len;
             uint32_t inc = flen;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -891,11 +877,31 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 // most the dropped bits, and the band (a prefix) stays a
                 // superset of every entry within T32 (1 + 2^-15) + 2^-120.
                 constexpr uint32_t SLOT = (uint32_t)B - 1;
-                uint32_t v[E];
+                // this lane's own (unsorted) entries g = lane*E + e: their FP32
+                // keys, and -- issued now, so that the sort below hides the
+                // latency -- the coordinates and original ids of their points
+                constexpr bool PREFETCH = E * (DIM + 1) <= 28;
+                uint32_t v[E], kr[E], sp[E];
+                float pc[PREFETCH ? E : 1][DIM];
+                uint32_t pid[PREFETCH ? E : 1];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int g = lane * E + e;
-                    v[e] = g < c0 ? (((uint32_t)(bi[g] >> 32) & ~SLOT) | (uint32_t)g) : 0xffffffffu;
+                    const uint64_t ent = g < c0 ? bi[g] : ~0ull;
+                    kr[e] = (uint32_t)(ent >> 32) & ~SLOT;
+                    sp[e] = (uint32_t)ent;
+                    v[e] = g < c0 ? (kr[e] | (uint32_t)g) : 0xffffffffu;
+                    if constexpr (PREFETCH) {
+                        const bool ok = g < c0 && KNN_GUARD(sp[e] < (uint64_t)a.n, 7);
+                        if (ok) {
+                            load_point<DIM>(a.xsort, sp[e], pc[e]);
+                            pid[e] = __ldg(&a.perm[sp[e]]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) pc[e][k] = 0.0f;
+                            pid[e] = 0;
+                        }
+                    }
                 }
                 warp_bitonic_u32<E>(v, lane);
                 KNN_PT(3);
@@ -912,7 +918,11 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
 #pragma unroll
                 for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(FULL, m, o);
                 KNN_PT(4);
-                // exact canonical distances and original ids of the band
+                // exact canonical distances and original ids of the band: each
+                // lane scores its own unsorted entries that lie in the band (the
+                // band is the set of keys <= tb, the same test as above) and
+                // parks them by buffer slot -- D over the buffer entry, the id in
+                // the histogram area -- where the sorted positions pick them up
                 float q[DIM];
                 int32_t qi[DIM];
 #pragma unroll
@@ -920,6 +930,44 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     q[k] = qc[i * QP + k];
                     qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
                 }
+                uint64_t *bw = buf + i * BS;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int g = lane * E + e;
+                    if (g < c0 && kr[e] <= tb) {
+                        float c[DIM];
+                        uint32_t id;
+                        if constexpr (PREFETCH) {
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) c[k] = pc[e][k];
+                            id = pid[e];
+                        } else {
+                            if (KNN_GUARD(sp[e] < (uint64_t)a.n, 7)) {
+                                load_point<DIM>(a.xsort, sp[e], c);
+                                id = a.perm[sp[e]];
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                                id = 0;
+                            }
+                        }
+                        uint64_t bits = 0;
+                        bool done = false;
+                        if (a.fixed_ok) {
+                            done = fsc != 0.0f && canon_d2_fixed_f32<DIM>(q, c, fsc, a.F, bits);
+                            if (!done) {
+                                int32_t ci[DIM];
+#pragma unroll
+                                for (int k = 0; k < DIM; ++k) ci[k] = to_fixed(c[k], a.F);
+                                done = canon_d2_fixed<DIM>(qi, ci, a.F, bits);
+                            }
+                        }
+                        if (!done) bits = canon_d2_fp64<DIM>(q, c);
+                        bw[g] = bits;
+                        hist[g] = id;
+                    }
+                }
+                __syncwarp();
                 uint64_t D[E];
                 uint32_t I[E];
 #pragma unroll
@@ -928,23 +976,12 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     D[e] = ~0ull;
                     I[e] = ~0u;
                     if (g < m) {
-                        const uint32_t s = (uint32_t)bi[v[e] & SLOT];
-                        float c[DIM];
-                        if (KNN_GUARD(s < (uint64_t)a.n, 7)) load_point<DIM>(a.xsort, s, c);
-                        else for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
-                        uint64_t bits = 0;
-                        bool done = false;
-                        if (a.fixed_ok) {
-                            int32_t ci[DIM];
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) ci[k] = to_fixed(c[k], a.F);
-                            done = canon_d2_fixed<DIM>(qi, ci, a.F, bits);
-                        }
-                        if (!done) bits = canon_d2_fp64<DIM>(q, c);
-                        D[e] = bits;
-                        I[e] = a.perm[s];
+                        const uint32_t slot = v[e] & SLOT;
+                        D[e] = bw[slot];
+                        I[e] = hist[slot];
                     }
                 }
+                __syncwarp();
                 if (lane == 0) st_band += (unsigned long long)m;
                 KNN_CNT(12, c0);
                 KNN_CNT(13, m);
@@ -967,7 +1004,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 for (int e = 0; e < E; ++e)
                     if (e == (K - 1) % E) dk = D[e];
                 dk = __shfl_sync(FULL, dk, (K - 1) / E);
-                const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
+                const float R = rcert[i];
                 bool certified = isinf(R);
                 if (!certified) {
                     const float R2 = __fmul_rd(__fmul_rd(R, R), 1.0f - 0x1p-20f);

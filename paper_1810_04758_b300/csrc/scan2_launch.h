@@ -1,0 +1,63 @@
+// scan2_launch.h -- host interface of the neighbour-cell scan kernel k_scan2
+// (scan2.cuh).  The kernel's instances for each dimension d are compiled in
+// their own translation unit (scan2_launch.cu built with KNN_SCAN2_DIM = d),
+// so the library builds in parallel; each unit holds its own copies of the
+// kernel's device tables and reports through the functions declared here.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace knn {
+
+struct ScanArgs;
+
+// Warps per CTA of k_scan2 (each works alone on its own work items).
+constexpr int S2_WARPS = 4;
+constexpr int S2_CTA = S2_WARPS * 32;
+
+// Row of a query in shared memory: coordinates, current threshold, sorted
+// position (as float bits), padded to a multiple of 4 floats (vector loads).
+__host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) & ~3; }
+
+// Entries of the per-item table of neighbour key parts (even, so that what
+// follows stays 16-byte aligned).
+__host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; }
+
+// Bytes of one warp's shared memory in k_scan2 (16-byte multiple):
+// candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
+// [QM][QP] f32, counts and sorted positions [QM] x 2, radix histogram [256],
+// squared face gaps [QM][3d] f32, certificate radii [QM] f32, the item's
+// cell and the level's extent [2d] i32.
+__host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
+{
+    return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
+            (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)QM * 4 + (size_t)2 * d * 4 + 15) &
+           ~(size_t)15;
+}
+
+// Queries per work item for a candidate buffer of 32*E entries: 16 with the
+// 64-entry buffers of K <= 32, 8 with larger ones (whose shared memory would
+// otherwise hold an SM to 2 CTAs).
+__host__ __device__ constexpr int scan2_queries_per_item(int E) { return E <= 2 ? 16 : 8; }
+
+// Launch k_scan2 for dimension DIM with buffers of 32*E entries (E = 2, 4
+// or 8) on stream s; mega selects the long-run walk that skips mega-tiles.
+// Returns cudaSuccess or the launch error; *nofit is set (and nothing is
+// launched) when the kernel cannot be resident on an SM.  *launches counts
+// the launches made.
+template <int DIM>
+cudaError_t scan2_launch(const ScanArgs &a, int E, bool mega, size_t smem, cudaStream_t s, int nsm, int dev,
+                         bool *nofit, int64_t *launches);
+
+// Checked builds (KNN_CHECKS): the failed-check word of this unit's kernels
+// (0 otherwise); clear = reset it to 0 after reading.
+template <int DIM>
+unsigned scan2_check_word(bool clear);
+
+// Diagnostic builds (KNN_PHASE_TIMING): add this unit's phase cycles and
+// event counts into out[0..32) (scan2_debug.cuh); reset = clear them.
+template <int DIM>
+cudaError_t scan2_debug_read(unsigned long long *out, bool reset);
+
+}  // namespace knn
