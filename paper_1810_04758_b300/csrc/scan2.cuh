@@ -371,7 +371,10 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
             acc = false;
             nnew = 0;
         }
-        if (lane == 0) qc[i * QP + DIM] = tnew;
+        if (lane == 0) {
+            qc[i * QP + DIM] = tnew;
+            qc[scan2_queries_per_item(E) * QP + i] = tnew;  // the thresholds' copy after the rows
+        }
         __syncwarp();
     }
     if (acc && KNN_GUARD(c0 >= 0 && c0 + __popc(bal & lanemask_lt()) < B, 4))
@@ -472,6 +475,56 @@ __device__ __forceinline__ void scan2_tile(const float (&c)[DIM], uint32_t s, bo
 // second batch may be tested against a threshold the first batch's insert
 // has since lowered; that only keeps extra entries (the buffer holds a
 // superset of what its threshold admits).
+// The acceptances of one query in a two-tile step (ballots accA / accB over
+// the lanes) go to its buffer.  The first tile's insert may have shrunk the
+// buffer and lowered the threshold, or marked the query for the general
+// kernel (threshold -1, count -1): the second tile is tested again, so that
+// nothing is appended to a marked query's buffer.
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_insert_pair(uint64_t *buf, float *qc, uint32_t *hist, int &my_cnt, int i,
+                                                  bool accA, bool accB, float dA, float dB, uint32_t sA,
+                                                  uint32_t sB, float ti, int K, int lane KNN_CNT_PARAM)
+{
+    KNN_CNT(11, 1);
+    KNN_CYC_BEGIN(ins);
+    const uint32_t balA = __ballot_sync(FULL, accA);
+    uint32_t balB = __ballot_sync(FULL, accB);
+    if (!(balA | balB)) return;
+    {
+        // common case: both tiles' acceptances fit in the buffer -- one read
+        // of the count, both appended, no threshold change in between
+        constexpr int B = 32 * E;
+        const int c0 = __shfl_sync(FULL, my_cnt, i);
+        const int nA = __popc(balA), nB = __popc(balB);
+        if (c0 >= 0 && c0 + nA + nB <= B) {
+            uint64_t *bi = buf + i * B;
+            const uint32_t lt = lanemask_lt();
+            const int pA = c0 + __popc(balA & lt), pB = c0 + nA + __popc(balB & lt);
+            if (accA && KNN_GUARD(pA < B, 4)) bi[pA] = ((uint64_t)__float_as_uint(dA) << 32) | sA;
+            if (accB && KNN_GUARD(pB < B, 4)) bi[pB] = ((uint64_t)__float_as_uint(dB) << 32) | sB;
+            if (lane == i) my_cnt = c0 + nA + nB;
+            KNN_CYC_END(ins, 15);
+            return;
+        }
+    }
+    // the buffer fills: tile A first (its insert may shrink the buffer)
+    float tB = ti;
+    if (balA) {
+        scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane KNN_CNT_ARG);
+        tB = qc[i * query_row_floats(DIM) + DIM];
+        balB = __ballot_sync(FULL, accB && dB <= tB);
+    }
+    if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB && dB <= tB, balB, dB, sB, K, tB, lane KNN_CNT_ARG);
+    KNN_CYC_END(ins, 15);
+}
+
+// Two tiles at once (lane = candidates sA and sB, NaN coordinates past the
+// end of the list): each query's row is read once for 64 candidates and its
+// two distances are computed together (packed FP32).  The second batch may
+// be tested against a threshold the first batch's insert has since lowered;
+// that only keeps extra entries (the buffer holds a superset of what its
+// threshold admits).  (Scoring two queries per iteration was measured
+// slower on every workload.)
 template <int DIM, int E>
 __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const float (&cB)[DIM], uint32_t sA,
                                                 uint32_t sB, uint32_t tmask, uint64_t *buf, float *qc,
@@ -491,22 +544,8 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
         const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
         const bool accB = dB <= ti && sB != qi_s;
         // one vote first for d >= 5, where a step usually accepts nothing
-        if (DIM < 5 || __any_sync(FULL, accA || accB)) {
-            KNN_CNT(11, 1);
-            const uint32_t balA = __ballot_sync(FULL, accA);
-            uint32_t balB = __ballot_sync(FULL, accB);
-            float tB = ti;
-            if (balA) {
-                scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accA, balA, dA, sA, K, ti, lane KNN_CNT_ARG);
-                // the insert may have shrunk the buffer and lowered the
-                // threshold, or marked the query for the general kernel
-                // (threshold -1, count -1): test the second tile again, so
-                // that nothing is appended to a marked query's buffer
-                tB = qc[i * query_row_floats(DIM) + DIM];
-                balB = __ballot_sync(FULL, accB && dB <= tB);
-            }
-            if (balB) scan2_insert<DIM, E>(buf, qc, hist, my_cnt, i, accB && dB <= tB, balB, dB, sB, K, tB, lane KNN_CNT_ARG);
-        }
+        if (DIM < 5 || __any_sync(FULL, accA || accB))
+            scan2_insert_pair<DIM, E>(buf, qc, hist, my_cnt, i, accA, accB, dA, dB, sA, sB, ti, K, lane KNN_CNT_ARG);
     }
 }
 
@@ -553,14 +592,18 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
     uint64_t *buf = (uint64_t *)wb;            // [QM][BS]  (d2_32 bits << 32 | sorted index)
     uint64_t *dil = buf + QM * BS;             // [3d] Morton bits of neighbour coordinates
     float *qc = (float *)(dil + dil_entries(DIM));  // [QM][QP] coords, threshold, sorted position
-    int *cnt = (int *)(qc + QM * QP);          // [QM]
+    // [QM] the thresholds again, contiguous (vector loads in the cell test);
+    // written wherever a row's threshold is
+    float *thrv = qc + QM * QP;
+    int *cnt = (int *)(thrv + QM);             // [QM]
     uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
     uint32_t *hist = qsv + QM;                 // [256]
-    // [QM][3d]: per dimension, the squared distance (rounded down) from the
+    // [3d][QM]: per dimension, the squared distance (rounded down) from each
     // query to the lower neighbour cell, 0 (same slab), to the upper one --
-    // indexed by the base-3 digit of a neighbour offset
+    // row 3k + g for the base-3 digit g of a neighbour offset in dimension k,
+    // queries contiguous (a lane reads every query's gap with vector loads)
     float *gsq = (float *)(hist + 256);
-    float *rcert = gsq + QM * GQ;              // [QM] certificate radius of each query
+    float *rcert = gsq + GQ * QM;              // [QM] certificate radius of each query
     int *cellv = (int *)(rcert + QM);          // [2d]
 
     unsigned long long st_cand = 0, st_band = 0;
@@ -640,9 +683,9 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 // q lies in [face(c), face(c+1)) exactly, so both gaps are >= 0
                 const float gl = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
                 const float gh = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
-                gsq[lane * GQ + 3 * k] = __fmul_rd(gl, gl);
-                gsq[lane * GQ + 3 * k + 1] = 0.0f;
-                gsq[lane * GQ + 3 * k + 2] = __fmul_rd(gh, gh);
+                gsq[(3 * k) * QM + lane] = __fmul_rd(gl, gl);
+                gsq[(3 * k + 1) * QM + lane] = 0.0f;
+                gsq[(3 * k + 2) * QM + lane] = __fmul_rd(gh, gh);
             }
             // start threshold: the certificate prefilter KNN_PREFILTER_R2 x R^2
             // (points beyond R cannot be in a certified answer), or the band
@@ -653,7 +696,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
                                    ? __int_as_float(0x7f800000)
                                    : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
-            qc[lane * QP + DIM] = fminf(thr0, a.seed[qsv[lane]]);
+            qc[lane * QP + DIM] = thrv[lane] = fminf(thr0, a.seed[qsv[lane]]);
             // the data position a candidate must not equal (none for R x S)
             qc[lane * QP + DIM + 1] = __uint_as_float(a.self ? qsv[lane] : 0xffffffffu);
         }
@@ -690,12 +733,35 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             // with a 2^-19 margin for FP32 rounding of candidate distances
             uint32_t cmask = 0;
             if (len) {
-                for (int i = 0; i < Q; ++i) {
-                    const float *g = gsq + i * GQ;
-                    float lb = g[goff[0]];
+                // lower bounds of all QM queries at once: the rows of this
+                // cell's digits, read as vectors, summed rounding down
+                float lb[QM];
 #pragma unroll
-                    for (int k = 1; k < DIM; ++k) lb = __fadd_rd(lb, g[goff[k]]);
-                    if (!(lb > qc[i * QP + DIM] * (1.0f + 0x1p-19f))) cmask |= 1u << i;
+                for (int k = 0; k < DIM; ++k) {
+                    const float4 *row = (const float4 *)(gsq + goff[k] * QM);
+#pragma unroll
+                    for (int v = 0; v < QM / 4; ++v) {
+                        const float4 t = row[v];
+                        if (k == 0) {
+                            lb[4 * v] = t.x;
+                            lb[4 * v + 1] = t.y;
+                            lb[4 * v + 2] = t.z;
+                            lb[4 * v + 3] = t.w;
+                        } else {
+                            lb[4 * v] = __fadd_rd(lb[4 * v], t.x);
+                            lb[4 * v + 1] = __fadd_rd(lb[4 * v + 1], t.y);
+                            lb[4 * v + 2] = __fadd_rd(lb[4 * v + 2], t.z);
+                            lb[4 * v + 3] = __fadd_rd(lb[4 * v + 3], t.w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < QM / 4; ++v) {
+                    const float4 t = ((const float4 *)thrv)[v];
+                    const float th[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (4 * v + j < Q && !(lb[4 * v + j] > th[j] * (1.0f + 0x1p-19f))) cmask |= 1u << (4 * v + j);
                 }
             }
             KNN_CNT(3, __popc(__ballot_sync(FULL, len != 0)));
@@ -819,6 +885,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
             };
             if (DIM >= S2_WIDE_DIM) {
                 for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+                    KNN_CYC_BEGIN(stp);
                     const bool vA = t0 + lane < total, vB = t0 + 32 + lane < total;
                     uint32_t sA, sB, cmA, cmB;
                     locate(t0 + lane, vA, sA, cmA);
@@ -836,6 +903,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                     if (vB && KNN_GUARD(sB < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sB, cB);
                     st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
                     KNN_ITEM_TILE(__popc(tmask) * 2);
+                    KNN_CYC_END(stp, 8);
                     scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
                 }
             } else {

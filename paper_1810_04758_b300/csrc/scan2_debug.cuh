@@ -28,6 +28,10 @@ __device__ unsigned long long g_count[16];
     do {                                     \
         cn_[i] += (unsigned long long)(v);   \
     } while (0)
+// cycles of a stretch of code added to event count i (the stretch's clock
+// reads stay in place: volatile)
+#define KNN_CYC_BEGIN(nm) const unsigned long long nm##_c0 = clock64()
+#define KNN_CYC_END(nm, i) KNN_CNT(i, clock64() - nm##_c0)
 // extra parameter / argument that hands the counters to helper functions
 #define KNN_CNT_PARAM , unsigned long long *cn_
 #define KNN_CNT_ARG , cn_
@@ -64,6 +68,10 @@ __device__ unsigned long long g_count[16];
     } while (0)
 #define KNN_CNT(i, v) \
     do {              \
+    } while (0)
+#define KNN_CYC_BEGIN(nm)
+#define KNN_CYC_END(nm, i) \
+    do {                   \
     } while (0)
 #define KNN_CNT_PARAM
 #define KNN_CNT_ARG

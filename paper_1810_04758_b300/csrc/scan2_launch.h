@@ -26,13 +26,14 @@ __host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; 
 
 // Bytes of one warp's shared memory in k_scan2 (16-byte multiple):
 // candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
-// [QM][QP] f32, counts and sorted positions [QM] x 2, radix histogram [256],
-// squared face gaps [QM][3d] f32, certificate radii [QM] f32, the item's
-// cell and the level's extent [2d] i32.
+// [QM][QP] f32, thresholds [QM] f32, counts and sorted positions [QM] x 2,
+// radix histogram [256], squared face gaps [3d][QM] f32, certificate radii
+// [QM] f32, the item's cell and the level's extent [2d] i32.
 __host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
 {
     return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
-            (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)QM * 4 + (size_t)2 * d * 4 + 15) &
+            (size_t)QM * 4 + (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)QM * 4 +
+            (size_t)2 * d * 4 + 15) &
            ~(size_t)15;
 }
 
