@@ -187,4 +187,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &t
     return off + x - v;
 }
 
+// Dense cell table of one grid level (used instead of the hash map when the
+// level's grid is small): entry c = (begin, end) of the run of the cell whose
+// level coordinates are c_0..c_{d-1}, index sum_k c_k * stride_k with
+// stride_0 = 1 and stride_k = stride_{k-1} * (cells in dimension k - 1);
+// cells without points hold (0, 0).
+struct DenseDims {
+    uint32_t stride[MAX_DIM];
+};
+
 }  // namespace knn

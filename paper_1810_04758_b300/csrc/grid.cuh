@@ -540,6 +540,23 @@ __global__ void k_run_begin(const uint32_t *__restrict__ flags, const uint32_t *
     }
 }
 
+// Dense cell table of a level (common.cuh, DenseDims): each run of the
+// level writes its (begin, end) at its cell's index; the table was zeroed.
+__global__ void k_dense_insert(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
+                               const uint32_t *ncells_p, int shift, int d, int nbits, DenseDims dims,
+                               uint2 *__restrict__ tab)
+{
+    const uint32_t ncells = *ncells_p;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const uint32_t b = begin[c], e = begin[c + 1];
+        int cell[MAX_DIM];
+        morton_decode(keys[b] >> shift, d, nbits, cell);
+        uint32_t idx = 0;
+        for (int k = 0; k < d; ++k) idx += (uint32_t)cell[k] * dims.stride[k];
+        tab[idx] = make_uint2(b, e);
+    }
+}
+
 // Insertion into the level hash map (common.cuh: layout and lookup).
 __global__ void k_hash_insert(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
                               const uint32_t *ncells_p, int shift, uint4 *slot, uint32_t hmask)

@@ -255,6 +255,7 @@ struct LevelTab {
     uint4 *slot = nullptr;
     uint32_t mask = 0;
     bool built = false;
+    uint2 *dense = nullptr;  // dense cell table (small grids) instead of the hash map
 };
 
 struct Pipeline {
@@ -764,13 +765,29 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
             scan(flags, rid, n);
             k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
+            // a level whose grid has at most max(2n, 2^16) cells gets a dense
+            // table (one load per neighbour lookup, no host readback here)
+            DenseDims dd{};
+            double G = 1.0;
+            for (int k = 0; k < d; ++k) {
+                dd.stride[k] = (uint32_t)G;
+                G *= (double)((hp.cmax0[k] >> L) + 1);
+            }
+            if (G <= std::max(2.0 * (double)n, 65536.0)) {
+                uint2 *tab = sc.get<uint2>("dense" + std::to_string(L), (size_t)G);
+                CK(cudaMemsetAsync(tab, 0, sizeof(uint2) * (size_t)G, s));
+                k_dense_insert<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, d, hp.bits - L,
+                                                                      dd, tab); ++launches;
+                tabs[L] = {nullptr, 0, true, tab};
+                return;
+            }
             uint32_t ncells = read1(small + 0);
             uint32_t H = 1;
             while (H < 2 * ncells) H <<= 1;
             uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
             CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
             k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
-            tabs[L] = {slot, H - 1, true};
+            tabs[L] = {slot, H - 1, true, nullptr};
         };
 
         // work items of a (level, position)-ordered list of sorted positions
@@ -889,6 +906,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 for (int L = 0; L < MAX_LEVELS; ++L) {
                     a.hslotL[L] = tabs[L].slot;
                     a.hmaskL[L] = tabs[L].mask;
+                    a.denseL[L] = tabs[L].dense;
                 }
                 a.fail = status;
                 a.seed = seed;
@@ -1789,7 +1807,7 @@ size_t noalloc_bytes_needed(int64_t n, int d)
     b += 2 * (size_t)n * 8 + 2 * (size_t)n * 4;  // keys, perm (+ alternates)
     b += 16 * ((size_t)n + 1) * 4;           // active lists, flags, scans, groups, fail
     b += (size_t)n * 8;                      // work items
-    b += 4 * H * 16;                         // cell hash maps of up to four grid levels
+    b += 4 * std::max(H * 16, std::max<size_t>(2 * (size_t)n, 65536) * 8);  // cell tables of up to four levels
     b += 3 * (size_t)n * 4 + 2 * (size_t)n;  // levels, level sort keys, window minima
     b += 256 * (((size_t)n + RS_TILE - 1) / RS_TILE) * 4 + 64 * 1024;  // histograms, sums, small
     b += sizeof(PrepReduce) + sizeof(GridParams) + 64 * 256;          // alignment slack

@@ -44,6 +44,7 @@ struct ScanArgs {
     uint32_t *counter;         // work-queue head
     const uint4 *hslotL[MAX_LEVELS];    // per-level hash maps (cell key -> run)
     uint32_t hmaskL[MAX_LEVELS];
+    const uint2 *denseL[MAX_LEVELS];    // per-level dense cell tables (null: the hash map)
     uint32_t *fail;            // [n] per sorted position: 0 certified, 1 not, 2 overflow
     float *seed;               // [n] per sorted position: FP32-filter threshold carried to the next pass
     int32_t *out_ids;          // [n][K]
@@ -239,7 +240,19 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 ok = ok && nb[k] >= 0 && nb[k] <= cmaxL[k];
             }
             uint2 rg = make_uint2(0, 0);
-            if (ok) rg = hash_lookup(a.hslotL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
+            if (ok) {
+                if (const uint2 *dt = a.denseL[level]) {
+                    uint32_t idx = 0, st = 1;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        idx += (uint32_t)nb[k] * st;
+                        st *= (uint32_t)cmaxL[k] + 1u;
+                    }
+                    rg = __ldg(&dt[idx]);
+                } else {
+                    rg = hash_lookup(a.hslotL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
+                }
+            }
             nb_range[t] = rg;
         }
         __syncthreads();

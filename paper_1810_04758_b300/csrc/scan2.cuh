@@ -625,6 +625,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
         const int nbits = a.bits - level;
         const uint4 *hslot = a.hslotL[level];
         const uint32_t hmask = a.hmaskL[level];
+        const uint2 *dtab = a.denseL[level];  // dense cell table, or null: the hash map
 
         if (lane < Q && KNN_GUARD(it.x + lane < (uint64_t)a.nactive, 0)) {
             uint32_t s = a.active[it.x + lane];
@@ -652,10 +653,12 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
         }
         __syncwarp();
         const int *cell = cellv, *cmaxL = cellv + DIM;
-        // neighbour keys by parts: dil[3k + g] holds the level-key bits of
-        // coordinate k of the neighbour at digit g (cell[k] + g - 1), so a
-        // neighbour's key is the OR of d table entries; bit 3k + g of nbad
-        // marks a coordinate outside the level's grid
+        // neighbour keys by parts: dil[3k + g] holds the part of coordinate k
+        // of the neighbour at digit g (cell[k] + g - 1) -- its level-key
+        // bits, or with a dense cell table its term c * stride_k of the
+        // table index -- so a neighbour's key or index is the sum of d table
+        // entries (the key parts occupy disjoint bits: sum = OR); bit 3k + g
+        // of nbad marks a coordinate outside the level's grid
         uint32_t nbad;
         {
             bool bad = false;
@@ -664,7 +667,13 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 const int c = cell[k] + lane % 3 - 1;
                 bad = c < 0 || c > cmaxL[k];
                 uint64_t v = 0;
-                for (int b = 0; b < nbits; ++b) v |= (uint64_t)((c >> b) & 1) << (b * DIM + k);
+                if (dtab) {
+                    uint32_t st = 1;
+                    for (int j = 0; j < k; ++j) st *= (uint32_t)cmaxL[j] + 1u;
+                    v = bad ? 0 : (uint64_t)((uint32_t)c * st);
+                } else {
+                    for (int b = 0; b < nbits; ++b) v |= (uint64_t)((c >> b) & 1) << (b * DIM + k);
+                }
                 dil[lane] = v;
             }
             nbad = __ballot_sync(FULL, bad);
@@ -718,11 +727,11 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
                 for (int k = 0; k < DIM; ++k) {
                     goff[k] = 3 * k + r % 3;
                     r /= 3;
-                    key |= dil[goff[k]];
+                    key += dil[goff[k]];
                     hit |= nbad >> goff[k];
                 }
                 if (!(hit & 1u)) {
-                    const uint2 rg = hash_lookup(hslot, hmask, key);
+                    const uint2 rg = dtab ? __ldg(&dtab[(uint32_t)key]) : hash_lookup(hslot, hmask, key);
                     rb = rg.x;
                     re = rg.y;
                 }
