@@ -637,9 +637,13 @@ def run_batched(args, rank, world, local_rank):
     outs_a = [(torch.empty((len(p), K), dtype=torch.int32, device=dev),
                torch.empty((len(p), K), dtype=torch.float64, device=dev)) for p, K in zip(pts, Ks)]
     outs_b = [(torch.empty_like(a), torch.empty_like(b)) for a, b in outs_a]
+    outs_c = [(torch.empty_like(a), torch.empty_like(b)) for a, b in outs_a]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = kj.Context(device=local_rank, stream=stream, workers=args.workers)
+    # the same batch with the joins' scans done together (one launch per
+    # (d, buffer size) group and pass over the union of their work items)
+    uctx = kj.Context(device=local_rank, stream=stream, batch_union=True)
 
     def plain():
         for p, K, (i, d) in zip(pts, Ks, outs_a):
@@ -649,6 +653,11 @@ def run_batched(args, rank, world, local_rank):
         jl = [kj.KnnjoinJob(p.data_ptr(), len(p), p.shape[1], K, i.data_ptr(), d.data_ptr())
               for p, K, (i, d) in zip(pts, Ks, outs_b)]
         kj.knnjoin_self_join_batch(ctx.ctx, jl)
+
+    def union():
+        jl = [kj.KnnjoinJob(p.data_ptr(), len(p), p.shape[1], K, i.data_ptr(), d.data_ptr())
+              for p, K, (i, d) in zip(pts, Ks, outs_c)]
+        kj.knnjoin_self_join_batch(uctx.ctx, jl)
 
     def timed(fn):
         ms = []
@@ -668,8 +677,11 @@ def run_batched(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         ms_plain = timed(plain)
         ms_batch = timed(batched)
+        ms_union = timed(union)
     same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs_a, outs_b))
+    same_u = all(torch.equal(a[0], c[0]) and torch.equal(a[1], c[1]) for a, c in zip(outs_a, outs_c))
     ctx.close()
+    uctx.close()
     if rank != 0:
         return 0
     value = world * nq / (ms_batch / 1e3)
@@ -686,6 +698,13 @@ def run_batched(args, rank, world, local_rank):
                           "how": "knnjoin_self_join per job, sequentially on one stream"},
         "speedup_vs_plain": ms_plain / ms_batch,
         "results_identical_to_plain": bool(same),
+        "union_scan": {"value": world * nq / (ms_union / 1e3), "ms_per_step": ms_union,
+                       "speedup_vs_plain": ms_plain / ms_union,
+                       "results_identical_to_plain": bool(same_u),
+                       "how": "knnjoin_self_join_batch with batch_union: every join's pass loop on "
+                              "its own stream and thread, each pass scanned by one launch per "
+                              "(d, buffer size) group over the union of the joins' work items, "
+                              "dense first across joins"},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

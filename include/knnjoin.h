@@ -91,7 +91,15 @@ typedef struct {
                                  run on high-priority streams, so their blocks are scheduled
                                  ahead of smaller joins sharing the GPU (shorter tail latency
                                  for large jobs, a little longer for small ones); 0 = off */
-    int reserved[4];
+    int batch_union;          /* knnjoin_self_join_batch: 1 = scan the batch's joins together.
+                                 Every join runs its own pass loop (index, density queue,
+                                 re-queue) on a stream and host thread of its own, and each
+                                 pass's scan is one launch per group of joins with the same
+                                 d and buffer size, over the union of their work items
+                                 ordered dense first across joins (Sec. 4.5 work queue).
+                                 0 = the worker pool runs whole joins concurrently.
+                                 Results are identical either way */
+    int reserved[3];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */

@@ -263,7 +263,9 @@ struct Pipeline {
     int nsm = 148;
     cudaStream_t s = nullptr;
     Scratch sc;
-    uint32_t *pinned = nullptr;      // small host readback area
+    uint32_t *pinned = nullptr;      // small host readback area (4 KB)
+    // word offset in `pinned` of the staging copy of the levels' cell tables
+    static constexpr int LEVELS_STAGING_WORD = 512;
     uint32_t *pinned_dev = nullptr;  // its device mapping (null: copy engine readbacks)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     knnjoin_stats stats{};
@@ -274,6 +276,7 @@ struct Pipeline {
     size_t out_chunk_bytes = 0;    // knnjoin_config.out_chunk_mb (0: automatic)
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
+    cudaEvent_t uev = nullptr;  // this join's work up to a union scan (batch_union)
     // worker pipelines: a join with at least BIG_JOB_ENTRIES output entries
     // and host outputs holds this token from its first pass until its kernels
     // end and releases it before copying its results to the host, so such
@@ -286,6 +289,9 @@ struct Pipeline {
     // parameters and, as they are built, the level hash maps; res_mode 2
     // makes run() answer R x S queries against what was kept
     int res_mode = 0;
+    // batched joins scanned together: the scan of each pass goes through this
+    // coordinator (one launch over the work items of every join of the batch)
+    struct UnionScan *uscan = nullptr;
     uint64_t *res_keys = nullptr;
     uint32_t *res_perm = nullptr;
     float *res_xsort = nullptr;
@@ -307,6 +313,7 @@ struct Pipeline {
         CK(cudaHostGetDevicePointer((void **)&pinned_dev, pinned, 0));
         for (auto &e : ev) CK(cudaEventCreate(&e));
         for (auto &e : evs) CK(cudaEventCreate(&e));
+        CK(cudaEventCreateWithFlags(&uev, cudaEventDisableTiming));
     }
     void release()
     {
@@ -317,6 +324,8 @@ struct Pipeline {
             if (e) cudaEventDestroy(e);
         for (auto &e : evs)
             if (e) cudaEventDestroy(e);
+        if (uev) cudaEventDestroy(uev);
+        uev = nullptr;
     }
 
     // run later joins on stream t (waits for this pipeline's work so far)
@@ -475,6 +484,161 @@ void dispatch_scan2(Pipeline &P, int d, int E, bool mega, const ScanArgs &a, siz
     ck(e, "scan kernel launch");
     if (nofit) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
 }
+
+// The scan kernel over several joins of dimension d (k_scan2_multi).
+void dispatch_scan2_multi(Pipeline &P, int d, int E, bool mega, const MultiScanArgs &p, size_t smem)
+{
+    bool nofit = false;
+    cudaError_t e;
+    switch (d) {
+    case 1: e = scan2_launch_multi<1>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 2: e = scan2_launch_multi<2>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 3: e = scan2_launch_multi<3>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 4: e = scan2_launch_multi<4>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 5: e = scan2_launch_multi<5>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 6: e = scan2_launch_multi<6>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 7: e = scan2_launch_multi<7>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    case 8: e = scan2_launch_multi<8>(p, E, mega, smem, P.s, P.nsm, P.device, &nofit, &P.launches); break;
+    default: fail(KNN_ERR_INVALID, "d out of range");
+    }
+    if (e == cudaErrorInvalidValue) fail(KNN_ERR_INVALID, "internal: bad buffer size");
+    ck(e, "batched scan kernel launch");
+    if (nofit) fail(KNN_ERR_INVALID, "scan kernel does not fit on an SM");
+}
+
+// Work items of up to S2_MULTI_JOBS joins as one queue: entry = job << 24 |
+// item, sort key = QM - (queries of the item), so that a stable sort puts
+// full items (dense cells) first across the joins, each join's own density
+// order kept among equal keys.
+struct UnionSrc {
+    const uint2 *items[S2_MULTI_JOBS];
+    uint32_t off[S2_MULTI_JOBS + 1];  // prefix sums of the joins' item counts
+    int njobs;
+    int qm;
+};
+
+__global__ void k_union_entries(const UnionSrc src, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+{
+    const uint32_t total = src.off[src.njobs];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int lo = 0, hi = src.njobs - 1;  // the job whose range holds t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (src.off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t item = t - src.off[lo];
+        const uint32_t q = src.items[lo][item].y & 0xffffu;
+        keys[t] = (uint32_t)src.qm - min(q, (uint32_t)src.qm);
+        vals[t] = ((uint32_t)lo << 24) | item;
+    }
+}
+
+// Batched joins scanned together (knnjoin_config.batch_union).  Every join
+// of the batch runs its own pass loop on its own stream and host thread; at
+// the scan of a pass it hands its arguments here and waits until every join
+// still running has done the same (or left), and the last to arrive makes
+// the launches: one per group of joins with the same d, buffer size and
+// long-run walk (at most S2_MULTI_JOBS joins each), over the union of their
+// work items ordered dense first across the joins (Sec. 4.5 work queue,
+// its high-density-first priority applied across joins).
+struct UnionScan {
+    struct Entry {
+        ScanArgs a;
+        int d, E;
+        bool mega;
+        size_t smem;
+        cudaEvent_t ready;
+    };
+    std::mutex mu;
+    std::condition_variable cv;
+    int members = 0, arrived = 0;
+    uint64_t round = 0;
+    std::vector<Entry> entries;
+    Pipeline co;  // the coordinator's stream and scratch (queue build, launches)
+    cudaEvent_t done = nullptr;
+    knnjoin_status err = KNN_OK;
+    std::string msg;
+    int64_t launches = 0, rounds = 0;
+
+    // (a round that closes early, launching for the joins present after a
+    // short wait, was measured slower: more, smaller launches)
+    void scan(Pipeline &P, int d, int E, bool mega, const ScanArgs &a, size_t smem)
+    {
+        CK(cudaEventRecord(P.uev, P.s));
+        std::unique_lock<std::mutex> lk(mu);
+        if (err != KNN_OK) fail(err, msg);
+        entries.push_back({a, d, E, mega, smem, P.uev});
+        ++arrived;
+        const uint64_t my = round;
+        if (arrived == members) launch_locked();
+        else cv.wait(lk, [&] { return round != my; });
+        if (err != KNN_OK) fail(err, msg);
+        CK(cudaStreamWaitEvent(P.s, done, 0));
+    }
+    // a join has finished (or failed): the others no longer wait for it
+    void leave()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        --members;
+        if (arrived > 0 && arrived == members) launch_locked();
+    }
+    void launch_locked()
+    {
+        try {
+            for (auto &e : entries) CK(cudaStreamWaitEvent(co.s, e.ready, 0));
+            std::map<std::tuple<int, int, bool>, std::vector<int>> groups;
+            for (int j = 0; j < (int)entries.size(); ++j)
+                groups[std::make_tuple(entries[j].d, entries[j].E, entries[j].mega)].push_back(j);
+            for (auto &g : groups) {
+                const std::vector<int> &idx = g.second;
+                const int d = std::get<0>(g.first), E = std::get<1>(g.first);
+                const bool mega = std::get<2>(g.first);
+                for (size_t c0 = 0; c0 < idx.size(); c0 += S2_MULTI_JOBS) {
+                    const int nj = (int)std::min<size_t>(S2_MULTI_JOBS, idx.size() - c0);
+                    std::unique_ptr<MultiScanArgs> p(new MultiScanArgs());
+                    memset(p.get(), 0, sizeof(MultiScanArgs));
+                    UnionSrc src;
+                    memset(&src, 0, sizeof(src));
+                    uint64_t total = 0;
+                    for (int j = 0; j < nj; ++j) {
+                        const ScanArgs &a = entries[idx[c0 + j]].a;
+                        p->jobs[j] = a;
+                        src.items[j] = a.items;
+                        src.off[j] = (uint32_t)total;
+                        if (a.nitems >= (1u << 24)) fail(KNN_ERR_INVALID, "batched scan: a join has too many work items");
+                        total += a.nitems;
+                    }
+                    if (total >= (1ull << 31)) fail(KNN_ERR_INVALID, "batched scan: too many work items");
+                    src.off[nj] = (uint32_t)total;
+                    src.njobs = nj;
+                    src.qm = scan2_queries_per_item(E);
+                    uint32_t *keys = co.sc.get<uint32_t>("u_keys", total), *vals = co.sc.get<uint32_t>("u_vals", total);
+                    uint32_t *k2 = co.sc.get<uint32_t>("u_keys2", total), *v2 = co.sc.get<uint32_t>("u_vals2", total);
+                    k_union_entries<<<grid_for((int64_t)total, 256, co.nsm), 256, 0, co.s>>>(src, keys, vals);
+                    ++launches;
+                    co.radix_sort<uint32_t>(keys, vals, k2, v2, (int64_t)total, bitlen32((uint32_t)src.qm));
+                    uint32_t *counter = co.sc.get<uint32_t>("u_counter", 1);
+                    CK(cudaMemsetAsync(counter, 0, 4, co.s));
+                    p->counter = counter;
+                    p->uitems = vals;
+                    p->nuitems = (uint32_t)total;
+                    p->njobs = nj;
+                    dispatch_scan2_multi(co, d, E, mega, *p, entries[idx[c0]].smem);
+                }
+            }
+            CK(cudaEventRecord(done, co.s));
+        } catch (const KnnError &e) {
+            err = e.st;
+            msg = e.msg;
+        }
+        ++round;
+        ++rounds;
+        arrived = 0;
+        entries.clear();
+        cv.notify_all();
+    }
+};
 
 #ifdef KNN_CHECKS
 // Failed-check words of every kernel unit (checked builds).
@@ -903,10 +1067,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.out_rows = chunked ? chunk_rows : nrows;
                 a.nq = nq;
                 a.counter = small + 3;
-                for (int L = 0; L < MAX_LEVELS; ++L) {
-                    a.hslotL[L] = tabs[L].slot;
-                    a.hmaskL[L] = tabs[L].mask;
-                    a.denseL[L] = tabs[L].dense;
+                {
+                    // the levels' cell tables, staged in the pinned readback
+                    // area (unchanged until this stream has synchronised)
+                    LevelRef *lr_host = (LevelRef *)(pinned + LEVELS_STAGING_WORD);
+                    for (int L = 0; L < MAX_LEVELS; ++L) lr_host[L] = {tabs[L].slot, tabs[L].dense, tabs[L].mask, 0u};
+                    LevelRef *lr_dev = sc.get<LevelRef>("levels", MAX_LEVELS);
+                    CK(cudaMemcpyAsync(lr_dev, lr_host, sizeof(LevelRef) * MAX_LEVELS, cudaMemcpyHostToDevice, s));
+                    a.levels = lr_dev;
                 }
                 a.fail = status;
                 a.seed = seed;
@@ -936,7 +1104,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 CK(cudaEventRecord(evs[0], s));
                 // skewed data, or a re-queued pass: walk long runs by
                 // mega-tiles (a query's box may hold long runs far from it)
-                if (fast) dispatch_scan2(*this, d, E2, pass > 0 || hp.finer > 0, a, smem2);
+                if (fast && uscan) uscan->scan(*this, d, E2, pass > 0 || hp.finer > 0, a, smem2);
+                else if (fast) dispatch_scan2(*this, d, E2, pass > 0 || hp.finer > 0, a, smem2);
                 else dispatch_scan(*this, d, a, smem1);
                 CK(cudaEventRecord(evs[1], s));
                 // the scan's time and candidate count, read after the pass's
@@ -1157,6 +1326,11 @@ struct knnjoin_ctx {
     TuneTable tune;
     std::vector<knnjoin_index *> indexes;  // live resident indexes (under g_idx_mu)
     std::mutex err_mu;                     // index queries writing err
+    // batches scanned together (batch_union): one pipeline (stream, scratch)
+    // per join of the largest batch so far, and the coordinator
+    std::mutex union_mu;                   // one such batch at a time
+    std::vector<std::unique_ptr<Pipeline>> upipes;
+    std::unique_ptr<UnionScan> ucoord;
 };
 
 // Resident index: one data set indexed once on its own pipeline (stream and
@@ -1297,6 +1471,71 @@ static void start_workers(knnjoin_ctx *ctx)
     }
 }
 
+// A batch with its joins scanned together (knnjoin_config.batch_union): T =
+// min(jobs, workers or 64) host threads, each with a pipeline of its own,
+// take joins in job order and run them, every pass's scan through the
+// coordinator (a thread stays a member of the union while it has joins to
+// run).  Blocks until every join is done; the first failure (in job order)
+// is reported.
+static void run_union_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs, int njobs)
+{
+    std::lock_guard<std::mutex> blk(ctx->union_mu);
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->ucoord) {
+        std::unique_ptr<UnionScan> u(new UnionScan());
+        cudaStream_t us = nullptr;
+        CK(cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking));
+        u->co.init(ctx->device, us, &ctx->al);
+        CK(cudaEventCreateWithFlags(&u->done, cudaEventDisableTiming));
+        ctx->ucoord = std::move(u);
+    }
+    const int T = std::min(njobs, ctx->cfg.workers > 0 ? ctx->cfg.workers : 64);
+    while ((int)ctx->upipes.size() < T) {
+        std::unique_ptr<Pipeline> P(new Pipeline());
+        cudaStream_t ps = nullptr;
+        CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+        P->init(ctx->device, ps, &ctx->al);
+        P->width_mult = ctx->main.width_mult;
+        P->tune = &ctx->tune;
+        P->policy = ctx->main.policy;
+        P->out_chunk_bytes = ctx->main.out_chunk_bytes;
+        ctx->upipes.push_back(std::move(P));
+    }
+    UnionScan &U = *ctx->ucoord;
+    U.members = T;
+    U.arrived = 0;
+    U.err = KNN_OK;
+    U.msg.clear();
+    U.entries.clear();
+    std::vector<knnjoin_status> st(njobs, KNN_OK);
+    std::vector<std::string> ms(njobs);
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+            cudaSetDevice(ctx->device);
+            Pipeline &P = *ctx->upipes[t];
+            P.uscan = &U;
+            for (int j = next++; j < njobs; j = next++) {
+                try {
+                    P.run(jobs[j].points, jobs[j].n, jobs[j].d, jobs[j].K, jobs[j].out_ids, jobs[j].out_dist);
+                } catch (const KnnError &e) {
+                    st[j] = e.st;
+                    ms[j] = e.msg;
+                } catch (const std::exception &e) {
+                    st[j] = KNN_ERR_INVALID;
+                    ms[j] = e.what();
+                }
+            }
+            P.uscan = nullptr;
+            U.leave();
+        });
+    for (auto &t : th) t.join();
+    for (int j = 0; j < njobs; ++j)
+        if (st[j] != KNN_OK) fail(st[j], "job " + std::to_string(j) + ": " + ms[j]);
+}
+
 // Run f, map its exception to a status and put the message in the
 // context's error string (or in *msg when given).
 static knnjoin_status guard(knnjoin_ctx *ctx, const std::function<void()> &f, std::string *msg = nullptr)
@@ -1424,6 +1663,23 @@ void knnjoin_destroy(knnjoin_ctx *ctx)
         cudaStreamSynchronize(w->pipe.s);
         cudaStreamDestroy(w->stream);
         if (w->stream_hi) cudaStreamDestroy(w->stream_hi);
+    }
+    for (auto &P : ctx->upipes) {
+        cudaStreamSynchronize(P->s);
+        cudaStream_t ps = P->s;
+        P->release();
+        cudaStreamSynchronize(ps);
+        cudaStreamDestroy(ps);
+    }
+    ctx->upipes.clear();
+    if (ctx->ucoord) {
+        cudaStream_t us = ctx->ucoord->co.s;
+        cudaStreamSynchronize(us);
+        ctx->ucoord->co.release();
+        if (ctx->ucoord->done) cudaEventDestroy(ctx->ucoord->done);
+        cudaStreamSynchronize(us);
+        cudaStreamDestroy(us);
+        ctx->ucoord.reset();
     }
     ctx->main.release();
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -1589,6 +1845,10 @@ knnjoin_status knnjoin_self_join_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs
         if (njobs == 0) return;
         // the caller's stream may hold work producing the inputs
         CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->cfg.batch_union) {
+            run_union_batch(ctx, jobs, njobs);
+            return;
+        }
         auto b = std::make_shared<Batch>();
         {
             std::lock_guard<std::mutex> lk(ctx->mu);

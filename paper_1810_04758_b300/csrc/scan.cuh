@@ -34,6 +34,14 @@ namespace knn {
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CTA = SCAN_WARPS * 32;
 
+// Cell table of one grid level: a dense table (small grids) or the hash map.
+struct LevelRef {
+    const uint4 *hslot;  // hash map slots (cell key -> run), or null
+    const uint2 *dense;  // dense table (cell index -> run), or null
+    uint32_t hmask;      // hash map capacity - 1
+    uint32_t pad;
+};
+
 struct ScanArgs {
     const float *xsort;        // [n][pad(d)] coordinates in key order (pad = 2, 4 or 8)
     const uint32_t *perm;      // key order -> original id
@@ -42,9 +50,7 @@ struct ScanArgs {
     const uint2 *items;        // (first active index, count | level << 16)
     uint32_t nitems;
     uint32_t *counter;         // work-queue head
-    const uint4 *hslotL[MAX_LEVELS];    // per-level hash maps (cell key -> run)
-    uint32_t hmaskL[MAX_LEVELS];
-    const uint2 *denseL[MAX_LEVELS];    // per-level dense cell tables (null: the hash map)
+    const LevelRef *levels;    // [MAX_LEVELS] cell tables of the grid levels (device memory)
     uint32_t *fail;            // [n] per sorted position: 0 certified, 1 not, 2 overflow
     float *seed;               // [n] per sorted position: FP32-filter threshold carried to the next pass
     int32_t *out_ids;          // [n][K]
@@ -70,6 +76,18 @@ struct ScanArgs {
     int64_t nactive;           // entries of `active`
     int CH;                    // staged candidates per chunk
     int noff;                  // 3^d
+};
+
+// Arguments of one scan launch over several joins (k_scan2_multi): their
+// work items in one queue, entry = job << 24 | item, and each join's
+// arguments, in the launch's parameter space.
+constexpr int S2_MULTI_JOBS = 64;
+struct MultiScanArgs {
+    uint32_t *counter;         // queue head
+    const uint32_t *uitems;    // [nuitems] queue entries
+    uint32_t nuitems;
+    int njobs;
+    ScanArgs jobs[S2_MULTI_JOBS];
 };
 
 __device__ __forceinline__ float band_thr(uint32_t tbits)
@@ -241,7 +259,8 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
             }
             uint2 rg = make_uint2(0, 0);
             if (ok) {
-                if (const uint2 *dt = a.denseL[level]) {
+                const LevelRef lr = a.levels[level];
+                if (const uint2 *dt = lr.dense) {
                     uint32_t idx = 0, st = 1;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) {
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                     }
                     rg = __ldg(&dt[idx]);
                 } else {
-                    rg = hash_lookup(a.hslotL[level], a.hmaskL[level], morton_encode(nb, DIM, nbits));
+                    rg = hash_lookup(lr.hslot, lr.hmask, morton_encode(nb, DIM, nbits));
                 }
             }
             nb_range[t] = rg;

@@ -570,557 +570,637 @@ __device__ __forceinline__ void scan2_super_tile(const ScanArgs &a, uint32_t sb,
     }
 }
 
-// MEGA selects the long-run walk: false, every super-tile tested in turn
-// (uniform data: the code of the hot loop stays as compiled without it);
-// true, mega-tiles tested first and skipped whole, two tiles per step
-// (density skew and re-queued passes, where one query's box can hold long
-// runs far from it).
-template <int DIM, int QM, int E, bool MEGA>
-__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(ScanArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int P = pad_dim(DIM);
-    constexpr int QP = query_row_floats(DIM);
-    constexpr int B = 32 * E;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int K = a.K, NOFF = a.noff;
-
-    // per-warp shared memory
-    constexpr int BS = B;
-    constexpr int GQ = 3 * DIM;  // squared-gap row of a query
-    unsigned char *wb = smem + warp * scan2_warp_bytes(DIM, QM, E);
-    uint64_t *buf = (uint64_t *)wb;            // [QM][BS]  (d2_32 bits << 32 | sorted index)
-    uint64_t *dil = buf + QM * BS;             // [3d] Morton bits of neighbour coordinates
-    float *qc = (float *)(dil + dil_entries(DIM));  // [QM][QP] coords, threshold, sorted position
-    // [QM] the thresholds again, contiguous (vector loads in the cell test);
-    // written wherever a row's threshold is
-    float *thrv = qc + QM * QP;
-    int *cnt = (int *)(thrv + QM);             // [QM]
-    uint32_t *qsv = (uint32_t *)(cnt + QM);    // [QM]
-    uint32_t *hist = qsv + QM;                 // [256]
+// Slices of one warp's shared memory in k_scan2 (sizes: scan2_warp_bytes).
+template <int DIM, int QM, int E>
+struct Scan2Warp {
+    uint64_t *buf;   // [QM][32E]  (d2_32 bits << 32 | sorted index)
+    uint64_t *dil;   // [3d] key parts (or dense index terms) of neighbour coordinates
+    float *qc;       // [QM][QP] coords, threshold, sorted position
+    float *thrv;     // [QM] the thresholds again, contiguous (vector loads in the cell test)
+    int *cnt;        // [QM]
+    uint32_t *qsv;   // [QM]
+    uint32_t *hist;  // [256]
     // [3d][QM]: per dimension, the squared distance (rounded down) from each
     // query to the lower neighbour cell, 0 (same slab), to the upper one --
     // row 3k + g for the base-3 digit g of a neighbour offset in dimension k,
     // queries contiguous (a lane reads every query's gap with vector loads)
-    float *gsq = (float *)(hist + 256);
-    float *rcert = gsq + GQ * QM;              // [QM] certificate radius of each query
-    int *cellv = (int *)(rcert + QM);          // [2d]
-
-    unsigned long long st_cand = 0, st_band = 0;
-    // 2^F as a float for the fixed-point distance from FP32 differences (0:
-    // F outside the normal exponent range, that path unused)
-    const float fsc = (a.fixed_ok && a.F >= -126 && a.F <= 127) ? __int_as_float((a.F + 127) << 23) : 0.0f;
-    KNN_PT_DECL;
-
-    for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1u);
-        item = __shfl_sync(FULL, item, 0);
-        if (item >= a.nitems) break;
-        KNN_ITEM_BEGIN;
-        const uint2 it = a.items[item];
-        const int Q = (int)(it.y & 0xffffu);
-        const int level = (int)(it.y >> 16);
-        const int shift = DIM * level;
-        const int nbits = a.bits - level;
-        const uint4 *hslot = a.hslotL[level];
-        const uint32_t hmask = a.hmaskL[level];
-        const uint2 *dtab = a.denseL[level];  // dense cell table, or null: the hash map
-
-        if (lane < Q && KNN_GUARD(it.x + lane < (uint64_t)a.nactive, 0)) {
-            uint32_t s = a.active[it.x + lane];
-            if (!KNN_GUARD(s < (uint64_t)a.nq, 1)) s = 0;
-            float c[DIM];
-            load_point<DIM>(a.qxsort, s, c);
-            qsv[lane] = s;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) qc[lane * QP + k] = c[k];
-        }
-        __syncwarp();
-        // the item's cell at its level and the level's last cell index, kept
-        // in shared memory (cellv) rather than registers across the scan
-        {
-            int cell[DIM];
-            morton_decode(a.qkeys[qsv[0]] >> shift, DIM, nbits, cell);
-            if (lane < DIM) {
-#pragma unroll
-                for (int k = 0; k < DIM; ++k)
-                    if (k == lane) {
-                        cellv[k] = cell[k];
-                        cellv[DIM + k] = a.cmax0[k] >> level;
-                    }
-            }
-        }
-        __syncwarp();
-        const int *cell = cellv, *cmaxL = cellv + DIM;
-        // neighbour keys by parts: dil[3k + g] holds the part of coordinate k
-        // of the neighbour at digit g (cell[k] + g - 1) -- its level-key
-        // bits, or with a dense cell table its term c * stride_k of the
-        // table index -- so a neighbour's key or index is the sum of d table
-        // entries (the key parts occupy disjoint bits: sum = OR); bit 3k + g
-        // of nbad marks a coordinate outside the level's grid
-        uint32_t nbad;
-        {
-            bool bad = false;
-            if (lane < 3 * DIM) {
-                const int k = lane / 3;
-                const int c = cell[k] + lane % 3 - 1;
-                bad = c < 0 || c > cmaxL[k];
-                uint64_t v = 0;
-                if (dtab) {
-                    uint32_t st = 1;
-                    for (int j = 0; j < k; ++j) st *= (uint32_t)cmaxL[j] + 1u;
-                    v = bad ? 0 : (uint64_t)((uint32_t)c * st);
-                } else {
-                    for (int b = 0; b < nbits; ++b) v |= (uint64_t)((c >> b) & 1) << (b * DIM + k);
-                }
-                dil[lane] = v;
-            }
-            nbad = __ballot_sync(FULL, bad);
-        }
-        __syncwarp();
-        // query state: threshold and sorted position sit in the query's row
-        // (one broadcast vector load gives a pair everything it needs); the
-        // buffer count lives in lane i's register for query i
-        int my_cnt = 0;
-        if (lane < Q) {
-            float q[DIM];
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) {
-                // q lies in [face(c), face(c+1)) exactly, so both gaps are >= 0
-                const float gl = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
-                const float gh = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
-                gsq[(3 * k) * QM + lane] = __fmul_rd(gl, gl);
-                gsq[(3 * k + 1) * QM + lane] = 0.0f;
-                gsq[(3 * k + 2) * QM + lane] = __fmul_rd(gh, gh);
-            }
-            // start threshold: the certificate prefilter KNN_PREFILTER_R2 x R^2
-            // (points beyond R cannot be in a certified answer), or the band
-            // of the K-th value an earlier pass found in a smaller box
-            // (contained in this one), whichever is lower
-            const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
-            rcert[lane] = R;
-            const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
-                                   ? __int_as_float(0x7f800000)
-                                   : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
-            qc[lane * QP + DIM] = thrv[lane] = fminf(thr0, a.seed[qsv[lane]]);
-            // the data position a candidate must not equal (none for R x S)
-            qc[lane * QP + DIM + 1] = __uint_as_float(a.self ? qsv[lane] : 0xffffffffu);
-        }
-        __syncwarp();
-
-        KNN_PT(0);
-        // a7 + a8
-        for (int ob = 0; ob < NOFF; ob += 32) {
-            const int o = ob + lane;
-            uint32_t rb = 0, re = 0;
-            int goff[DIM];  // offset of this cell's squared gap, per dimension
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) goff[k] = 3 * k + 1;
-            if (o < NOFF) {
-                int r = __ldg(&g_nb_order[nb_order_offset(DIM) + o]);
-                uint64_t key = 0;
-                uint32_t hit = 0;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    goff[k] = 3 * k + r % 3;
-                    r /= 3;
-                    key += dil[goff[k]];
-                    hit |= nbad >> goff[k];
-                }
-                if (!(hit & 1u)) {
-                    const uint2 rg = dtab ? __ldg(&dtab[(uint32_t)key]) : hash_lookup(hslot, hmask, key);
-                    rb = rg.x;
-                    re = rg.y;
-                }
-            }
-            const uint32_t len = re - rb;
-            // queries this cell can still serve: rounded-down squared distance
-            // from the query to the cell's box, against the query's threshold
-            // with a 2^-19 margin for FP32 rounding of candidate distances
-            uint32_t cmask = 0;
-            if (len) {
-                // lower bounds of all QM queries at once: the rows of this
-                // cell's digits, read as vectors, summed rounding down
-                float lb[QM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    const float4 *row = (const float4 *)(gsq + goff[k] * QM);
-#pragma unroll
-                    for (int v = 0; v < QM / 4; ++v) {
-                        const float4 t = row[v];
-                        if (k == 0) {
-                            lb[4 * v] = t.x;
-                            lb[4 * v + 1] = t.y;
-                            lb[4 * v + 2] = t.z;
-                            lb[4 * v + 3] = t.w;
-                        } else {
-                            lb[4 * v] = __fadd_rd(lb[4 * v], t.x);
-                            lb[4 * v + 1] = __fadd_rd(lb[4 * v + 1], t.y);
-                            lb[4 * v + 2] = __fadd_rd(lb[4 * v + 2], t.z);
-                            lb[4 * v + 3] = __fadd_rd(lb[4 * v + 3], t.w);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < QM / 4; ++v) {
-                    const float4 t = ((const float4 *)thrv)[v];
-                    const float th[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (4 * v + j < Q && !(lb[4 * v + j] > th[j] * (1.0f + 0x1p-19f))) cmask |= 1u << (4 * v + j);
-                }
-            }
-            KNN_CNT(3, __popc(__ballot_sync(FULL, len != 0)));
-            KNN_CNT(4, __popc(__ballot_sync(FULL, cmask != 0)));
-            // long runs first, outside the flattened scan
-            const bool bigcell = len >= S2_BIG;
-            const uint32_t bigmask = __ballot_sync(FULL, bigcell && cmask != 0);
-            // long runs: super-tiles, starting at the one that holds the
-            // item's first query when it lies in the run (nearby in key order
-            // is mostly nearby in space) and alternating outwards
-            for (uint32_t bm = bigmask; bm; bm &= bm - 1) {
-                const int src = __ffs(bm) - 1;
-                const uint32_t cb = __shfl_sync(FULL, rb, src), ce = __shfl_sync(FULL, re, src);
-                const uint32_t cmk = __shfl_sync(FULL, cmask, src);
-                const int nst = (int)((ce - cb + S2_SUPER - 1) / S2_SUPER);
-                const uint32_t sq = qsv[0];
-                const int u0 = (a.self && sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
-                if constexpr (MEGA) {
-                    // two cursors walk outwards from u0 (hi up, lo down),
-                    // taking turns; entering a mega-tile, a cursor tests its
-                    // box first and jumps over it when no query can use it
-                    // (thresholds only fall, so a skipped group stays useless)
-                    int hi = u0, lo = u0 - 1, mhi = -1, mlo = -1;
-                    bool up = true;
-                    while (hi < nst || lo >= 0) {
-                        int u;
-                        if (lo < 0 || (up && hi < nst)) {
-                            u = hi;
-                            const int M = u / S2_MEGA;
-                            if (M != mhi) {
-                                mhi = M;
-                                const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
-                                const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
-                                if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
-                                    hi = (M + 1) * S2_MEGA;
-                                    up = false;
-                                    continue;
-                                }
-                            }
-                            ++hi;
-                        } else {
-                            u = lo;
-                            const int M = u / S2_MEGA;
-                            if (M != mlo) {
-                                mlo = M;
-                                const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
-                                const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
-                                if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
-                                    lo = M * S2_MEGA - 1;
-                                    up = true;
-                                    continue;
-                                }
-                            }
-                            --lo;
-                        }
-                        up = !up;
-                        const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
-                        const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
-                        const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
-                        KNN_CNT(7, 1);
-                        if (!smask) continue;
-                        KNN_CNT(6, 1);
-                        if (DIM >= S2_WIDE_DIM) {
-                            // two tiles per step, as for the flattened runs
-                            for (uint32_t t0 = sb; t0 < se; t0 += 64) {
-                                const bool vA = t0 + lane < se, vB = t0 + 32 + lane < se;
-                                const uint32_t sA = vA ? t0 + lane : 0u, sB = vB ? t0 + 32 + lane : 0u;
-                                float cA[DIM], cB[DIM];
-#pragma unroll
-                                for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
-                                if (vA) load_point<DIM>(a.xsort, sA, cA);
-                                if (vB) load_point<DIM>(a.xsort, sB, cB);
-                                st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
-                                KNN_ITEM_TILE(__popc(smask) * 2);
-                                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
-                            }
-                        } else {
-                            scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
-                        }
-                    }
-                } else {
-                    // super-tiles alternating outwards from u0, one tile per step
-                    for (int j = 0, left = nst; left > 0; ++j) {
-                        const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
-                        if (u < 0 || u >= nst) continue;
-                        --left;
-                        const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
-                        const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
-                        const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
-                        if (!smask) continue;
-                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
-                    }
-                }
-            }
-            // (cells that no query of the item can use stay out of the
-            // flattened list)
-            const uint32_t flen = (bigcell || cmask == 0) ? 0u : len;
-            uint32_t inc = flen;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                uint32_t y = __shfl_up_sync(FULL, inc, d);
-                if (lane >= d) inc += y;
-            }
-            const uint32_t exc = inc - flen;
-            const uint32_t total = __shfl_sync(FULL, inc, 31);
-            KNN_CNT(5, total);
-            KNN_PT(1);
-            // flattened position t -> (sorted position, cell's query mask)
-            auto locate = [&](uint32_t t, bool valid, uint32_t &sp, uint32_t &cmo) {
-                int src = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    uint32_t ex = __shfl_sync(FULL, exc, src + step);
-                    if (ex <= t) src += step;
-                }
-                const uint32_t sb = __shfl_sync(FULL, rb, src);
-                const uint32_t se = __shfl_sync(FULL, exc, src);
-                sp = valid ? sb + (t - se) : 0u;
-                const uint32_t cm = __shfl_sync(FULL, cmask, src);  // every lane takes part
-                cmo = valid ? cm : 0u;
-            };
-            if (DIM >= S2_WIDE_DIM) {
-                for (uint32_t t0 = 0; t0 < total; t0 += 64) {
-                    KNN_CYC_BEGIN(stp);
-                    const bool vA = t0 + lane < total, vB = t0 + 32 + lane < total;
-                    uint32_t sA, sB, cmA, cmB;
-                    locate(t0 + lane, vA, sA, cmA);
-                    locate(t0 + 32 + lane, vB, sB, cmB);
-                    const uint32_t tmask = __reduce_or_sync(FULL, cmA | cmB);
-                    KNN_CNT(0, 1);
-                    KNN_CNT(1, __popc(tmask));
-                    KNN_CNT(2, tmask == 0);
-                    // lanes past the end get NaN coordinates: every distance
-                    // comparison with them is false
-                    float cA[DIM], cB[DIM];
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
-                    if (vA && KNN_GUARD(sA < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sA, cA);
-                    if (vB && KNN_GUARD(sB < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sB, cB);
-                    st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
-                    KNN_ITEM_TILE(__popc(tmask) * 2);
-                    KNN_CYC_END(stp, 8);
-                    scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
-                }
-            } else {
-                for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-                    const bool valid = t0 + lane < total;
-                    uint32_t s, cmo;
-                    locate(t0 + lane, valid, s, cmo);
-                    const uint32_t tmask = __reduce_or_sync(FULL, cmo);
-                    float c[DIM];
-                    if (valid) {
-                        load_point<DIM>(a.xsort, s, c);
-                        st_cand += (unsigned long long)__popc(tmask);  // distances evaluated
-                        KNN_ITEM_TILE(__popc(tmask));
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
-                    }
-                    scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
-                }
-            }
-            KNN_PT(2);
-        }
-        __syncwarp();
-
-        if (lane < Q) cnt[lane] = my_cnt;
-        __syncwarp();
-
-        // a9 - a11, one query at a time, whole warp
-        for (int i = 0; i < Q; ++i) {
-            const int c0 = cnt[i];
-            uint32_t flag = 1;
-            if (c0 < 0) {
-                flag = 2;
-            } else if (c0 >= K) {
-                const uint64_t *bi = buf + i * BS;
-                // whole buffer in registers (blocked: entry g = lane*E + e) as
-                // 32-bit words: the FP32 key with its low bits replaced by the
-                // buffer slot.  Sorted, entry K-1 bounds T32 from above by at
-                // most the dropped bits, and the band (a prefix) stays a
-                // superset of every entry within T32 (1 + 2^-15) + 2^-120.
-                constexpr uint32_t SLOT = (uint32_t)B - 1;
-                // this lane's own (unsorted) entries g = lane*E + e: their FP32
-                // keys, and -- issued now, so that the sort below hides the
-                // latency -- the coordinates and original ids of their points
-                constexpr bool PREFETCH = E * (DIM + 1) <= 28;
-                uint32_t v[E], kr[E], sp[E];
-                float pc[PREFETCH ? E : 1][DIM];
-                uint32_t pid[PREFETCH ? E : 1];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int g = lane * E + e;
-                    const uint64_t ent = g < c0 ? bi[g] : ~0ull;
-                    kr[e] = (uint32_t)(ent >> 32) & ~SLOT;
-                    sp[e] = (uint32_t)ent;
-                    v[e] = g < c0 ? (kr[e] | (uint32_t)g) : 0xffffffffu;
-                    if constexpr (PREFETCH) {
-                        const bool ok = g < c0 && KNN_GUARD(sp[e] < (uint64_t)a.n, 7);
-                        if (ok) {
-                            load_point<DIM>(a.xsort, sp[e], pc[e]);
-                            pid[e] = __ldg(&a.perm[sp[e]]);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) pc[e][k] = 0.0f;
-                            pid[e] = 0;
-                        }
-                    }
-                }
-                warp_bitonic_u32<E>(v, lane);
-                KNN_PT(3);
-                uint32_t vk = 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (e == (K - 1) % E) vk = v[e];
-                vk = __shfl_sync(FULL, vk, (K - 1) / E);
-                const uint32_t tb = __float_as_uint(band_thr(vk | SLOT)) & ~SLOT;
-                int mine = 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e) mine += (lane * E + e < c0 && (v[e] & ~SLOT) <= tb) ? 1 : 0;
-                int m = mine;
-#pragma unroll
-                for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(FULL, m, o);
-                KNN_PT(4);
-                // exact canonical distances and original ids of the band: each
-                // lane scores its own unsorted entries that lie in the band (the
-                // band is the set of keys <= tb, the same test as above) and
-                // parks them by buffer slot -- D over the buffer entry, the id in
-                // the histogram area -- where the sorted positions pick them up
-                float q[DIM];
-                int32_t qi[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    q[k] = qc[i * QP + k];
-                    qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
-                }
-                uint64_t *bw = buf + i * BS;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int g = lane * E + e;
-                    if (g < c0 && kr[e] <= tb) {
-                        float c[DIM];
-                        uint32_t id;
-                        if constexpr (PREFETCH) {
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) c[k] = pc[e][k];
-                            id = pid[e];
-                        } else {
-                            if (KNN_GUARD(sp[e] < (uint64_t)a.n, 7)) {
-                                load_point<DIM>(a.xsort, sp[e], c);
-                                id = a.perm[sp[e]];
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
-                                id = 0;
-                            }
-                        }
-                        uint64_t bits = 0;
-                        bool done = false;
-                        if (a.fixed_ok) {
-                            done = fsc != 0.0f && canon_d2_fixed_f32<DIM>(q, c, fsc, a.F, bits);
-                            if (!done) {
-                                int32_t ci[DIM];
-#pragma unroll
-                                for (int k = 0; k < DIM; ++k) ci[k] = to_fixed(c[k], a.F);
-                                done = canon_d2_fixed<DIM>(qi, ci, a.F, bits);
-                            }
-                        }
-                        if (!done) bits = canon_d2_fp64<DIM>(q, c);
-                        bw[g] = bits;
-                        hist[g] = id;
-                    }
-                }
-                __syncwarp();
-                uint64_t D[E];
-                uint32_t I[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int g = lane * E + e;
-                    D[e] = ~0ull;
-                    I[e] = ~0u;
-                    if (g < m) {
-                        const uint32_t slot = v[e] & SLOT;
-                        D[e] = bw[slot];
-                        I[e] = hist[slot];
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) st_band += (unsigned long long)m;
-                KNN_CNT(12, c0);
-                KNN_CNT(13, m);
-                KNN_PT(5);
-                // the FP32 order is the exact order unless two near-equal
-                // values swap; check neighbours, re-sort by (D, id) if needed
-                bool inv = false;
-#pragma unroll
-                for (int e = 0; e + 1 < E; ++e)
-                    inv = inv || (lane * E + e + 1 < m && xless(D[e + 1], I[e + 1], D[e], I[e]));
-                const uint64_t nd = __shfl_down_sync(FULL, D[0], 1);
-                const uint32_t ni = __shfl_down_sync(FULL, I[0], 1);
-                inv = inv || (lane < 31 && (lane + 1) * E < m && xless(nd, ni, D[E - 1], I[E - 1]));
-                if (__any_sync(FULL, inv)) {
-                    KNN_CNT(14, 1);
-                    warp_bitonic<E>(D, I, lane);
-                }
-                uint64_t dk = 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (e == (K - 1) % E) dk = D[e];
-                dk = __shfl_sync(FULL, dk, (K - 1) / E);
-                const float R = rcert[i];
-                bool certified = isinf(R);
-                if (!certified) {
-                    const float R2 = __fmul_rd(__fmul_rd(R, R), 1.0f - 0x1p-20f);
-                    certified = dk < f32_to_f64_bits_floor(R2);
-                }
-                KNN_PT(6);
-                // not certified: the K-th value bounds the next pass's threshold
-                if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
-                if (certified) {
-                    flag = 0;
-                    const int64_t rowq = (int64_t)a.qperm[qsv[i]] - a.row0;
-                    const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
-                    const bool rowok = KNN_GUARD(rowin, 5) && rowin;
-                    const int64_t row = rowq * K;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const int g = lane * E + e;
-                        if (g < K && rowok) {
-                            a.out_ids[row + g] = (int32_t)I[e];
-                            a.out_dist[row + g] = __longlong_as_double((long long)D[e]);  // D; k_sqrt_rows converts
-                        }
-                    }
-                }
-            }
-            if (lane == 0) a.fail[qsv[i]] = flag;
-            KNN_PT(7);
-        }
-        __syncwarp();
-        KNN_ITEM_END(Q);
+    float *gsq;
+    float *rcert;    // [QM] certificate radius of each query
+    int *cellv;      // [2d] the item's cell and the level's extent
+    __device__ __forceinline__ explicit Scan2Warp(unsigned char *wb)
+    {
+        buf = (uint64_t *)wb;
+        dil = buf + QM * 32 * E;
+        qc = (float *)(dil + dil_entries(DIM));
+        thrv = qc + QM * query_row_floats(DIM);
+        cnt = (int *)(thrv + QM);
+        qsv = (uint32_t *)(cnt + QM);
+        hist = qsv + QM;
+        gsq = (float *)(hist + 256);
+        rcert = gsq + 3 * DIM * QM;
+        cellv = (int *)(rcert + QM);
     }
-    KNN_PT_FLUSH;
+};
+
+// 2^F as a float for the fixed-point distance from FP32 differences (0: F
+// outside the normal exponent range, that path unused).
+__device__ __forceinline__ float scan2_fixed_scale(const ScanArgs &a)
+{
+    return (a.fixed_ok && a.F >= -126 && a.F <= 127) ? __int_as_float((a.F + 127) << 23) : 0.0f;
+}
+
+// A warp's candidate and band counts into the join's statistics.
+__device__ __forceinline__ void scan2_flush_stats(const ScanArgs &a, unsigned long long st_cand,
+                                                  unsigned long long st_band, int lane)
+{
     for (int o = 16; o; o >>= 1) {
         st_cand += __shfl_xor_sync(FULL, st_cand, o);
         st_band += __shfl_xor_sync(FULL, st_band, o);
     }
     if (lane == 0) {
-        atomicAdd(&a.stats[0], st_cand);
+        if (st_cand) atomicAdd(&a.stats[0], st_cand);
         if (st_band) atomicAdd(&a.stats[2], st_band);
     }
 }
+
+// MEGA selects the long-run walk: false, every super-tile tested in turn
+// (uniform data: the code of the hot loop stays as compiled without it);
+// true, mega-tiles tested first and skipped whole, two tiles per step
+// (density skew and re-queued passes, where one query's box can hold long
+// runs far from it).
+// One work item (a7-a11): its queries against their neighbour cells.
+template <int DIM, int QM, int E, bool MEGA>
+__device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, const Scan2Warp<DIM, QM, E> &w,
+                                           int lane, float fsc, unsigned long long &st_cand,
+                                           unsigned long long &st_band KNN_CNT_PARAM)
+{
+    constexpr int P = pad_dim(DIM);
+    constexpr int QP = query_row_floats(DIM);
+    constexpr int B = 32 * E;
+    constexpr int BS = B;
+    constexpr int GQ = 3 * DIM;
+    (void)P;
+    (void)GQ;
+    const int K = a.K, NOFF = a.noff;
+    uint64_t *const buf = w.buf;
+    uint64_t *const dil = w.dil;
+    float *const qc = w.qc;
+    float *const thrv = w.thrv;
+    int *const cnt = w.cnt;
+    uint32_t *const qsv = w.qsv;
+    uint32_t *const hist = w.hist;
+    float *const gsq = w.gsq;
+    float *const rcert = w.rcert;
+    int *const cellv = w.cellv;
+    KNN_ITEM_BEGIN;
+    const uint2 it = a.items[item];
+    const int Q = (int)(it.y & 0xffffu);
+    const int level = (int)(it.y >> 16);
+    const int shift = DIM * level;
+    const int nbits = a.bits - level;
+    const LevelRef lr = a.levels[level];
+    const uint4 *hslot = lr.hslot;
+    const uint32_t hmask = lr.hmask;
+    const uint2 *dtab = lr.dense;  // dense cell table, or null: the hash map
+
+    if (lane < Q && KNN_GUARD(it.x + lane < (uint64_t)a.nactive, 0)) {
+        uint32_t s = a.active[it.x + lane];
+        if (!KNN_GUARD(s < (uint64_t)a.nq, 1)) s = 0;
+        float c[DIM];
+        load_point<DIM>(a.qxsort, s, c);
+        qsv[lane] = s;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) qc[lane * QP + k] = c[k];
+    }
+    __syncwarp();
+    // the item's cell at its level and the level's last cell index, kept
+    // in shared memory (cellv) rather than registers across the scan
+    {
+        int cell[DIM];
+        morton_decode(a.qkeys[qsv[0]] >> shift, DIM, nbits, cell);
+        if (lane < DIM) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+                if (k == lane) {
+                    cellv[k] = cell[k];
+                    cellv[DIM + k] = a.cmax0[k] >> level;
+                }
+        }
+    }
+    __syncwarp();
+    const int *cell = cellv, *cmaxL = cellv + DIM;
+    // neighbour keys by parts: dil[3k + g] holds the part of coordinate k
+    // of the neighbour at digit g (cell[k] + g - 1) -- its level-key
+    // bits, or with a dense cell table its term c * stride_k of the
+    // table index -- so a neighbour's key or index is the sum of d table
+    // entries (the key parts occupy disjoint bits: sum = OR); bit 3k + g
+    // of nbad marks a coordinate outside the level's grid
+    uint32_t nbad;
+    {
+        bool bad = false;
+        if (lane < 3 * DIM) {
+            const int k = lane / 3;
+            const int c = cell[k] + lane % 3 - 1;
+            bad = c < 0 || c > cmaxL[k];
+            uint64_t v = 0;
+            if (dtab) {
+                uint32_t st = 1;
+                for (int j = 0; j < k; ++j) st *= (uint32_t)cmaxL[j] + 1u;
+                v = bad ? 0 : (uint64_t)((uint32_t)c * st);
+            } else {
+                for (int b = 0; b < nbits; ++b) v |= (uint64_t)((c >> b) & 1) << (b * DIM + k);
+            }
+            dil[lane] = v;
+        }
+        nbad = __ballot_sync(FULL, bad);
+    }
+    __syncwarp();
+    // query state: threshold and sorted position sit in the query's row
+    // (one broadcast vector load gives a pair everything it needs); the
+    // buffer count lives in lane i's register for query i
+    int my_cnt = 0;
+    if (lane < Q) {
+        float q[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) q[k] = qc[lane * QP + k];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            // q lies in [face(c), face(c+1)) exactly, so both gaps are >= 0
+            const float gl = __fsub_rd(q[k], face_of(cell[k] << level, a.lo[k], a.w0));
+            const float gh = __fsub_rd(face_of((cell[k] + 1) << level, a.lo[k], a.w0), q[k]);
+            gsq[(3 * k) * QM + lane] = __fmul_rd(gl, gl);
+            gsq[(3 * k + 1) * QM + lane] = 0.0f;
+            gsq[(3 * k + 2) * QM + lane] = __fmul_rd(gh, gh);
+        }
+        // start threshold: the certificate prefilter KNN_PREFILTER_R2 x R^2
+        // (points beyond R cannot be in a certified answer), or the band
+        // of the K-th value an earlier pass found in a smaller box
+        // (contained in this one), whichever is lower
+        const float R = cert_radius<DIM>(q, cell, cmaxL, a, level);
+        rcert[lane] = R;
+        const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
+                               ? __int_as_float(0x7f800000)
+                               : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
+        qc[lane * QP + DIM] = thrv[lane] = fminf(thr0, a.seed[qsv[lane]]);
+        // the data position a candidate must not equal (none for R x S)
+        qc[lane * QP + DIM + 1] = __uint_as_float(a.self ? qsv[lane] : 0xffffffffu);
+    }
+    __syncwarp();
+
+    KNN_PT(0);
+    // a7 + a8
+    for (int ob = 0; ob < NOFF; ob += 32) {
+        const int o = ob + lane;
+        uint32_t rb = 0, re = 0;
+        int goff[DIM];  // offset of this cell's squared gap, per dimension
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) goff[k] = 3 * k + 1;
+        if (o < NOFF) {
+            int r = __ldg(&g_nb_order[nb_order_offset(DIM) + o]);
+            uint64_t key = 0;
+            uint32_t hit = 0;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                goff[k] = 3 * k + r % 3;
+                r /= 3;
+                key += dil[goff[k]];
+                hit |= nbad >> goff[k];
+            }
+            if (!(hit & 1u)) {
+                const uint2 rg = dtab ? __ldg(&dtab[(uint32_t)key]) : hash_lookup(hslot, hmask, key);
+                rb = rg.x;
+                re = rg.y;
+            }
+        }
+        const uint32_t len = re - rb;
+        // queries this cell can still serve: rounded-down squared distance
+        // from the query to the cell's box, against the query's threshold
+        // with a 2^-19 margin for FP32 rounding of candidate distances
+        uint32_t cmask = 0;
+        if (len) {
+            // lower bounds of all QM queries at once: the rows of this
+            // cell's digits, read as vectors, summed rounding down
+            float lb[QM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const float4 *row = (const float4 *)(gsq + goff[k] * QM);
+#pragma unroll
+                for (int v = 0; v < QM / 4; ++v) {
+                    const float4 t = row[v];
+                    if (k == 0) {
+                        lb[4 * v] = t.x;
+                        lb[4 * v + 1] = t.y;
+                        lb[4 * v + 2] = t.z;
+                        lb[4 * v + 3] = t.w;
+                    } else {
+                        lb[4 * v] = __fadd_rd(lb[4 * v], t.x);
+                        lb[4 * v + 1] = __fadd_rd(lb[4 * v + 1], t.y);
+                        lb[4 * v + 2] = __fadd_rd(lb[4 * v + 2], t.z);
+                        lb[4 * v + 3] = __fadd_rd(lb[4 * v + 3], t.w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < QM / 4; ++v) {
+                const float4 t = ((const float4 *)thrv)[v];
+                const float th[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * v + j < Q && !(lb[4 * v + j] > th[j] * (1.0f + 0x1p-19f))) cmask |= 1u << (4 * v + j);
+            }
+        }
+        KNN_CNT(3, __popc(__ballot_sync(FULL, len != 0)));
+        KNN_CNT(4, __popc(__ballot_sync(FULL, cmask != 0)));
+        // long runs first, outside the flattened scan
+        const bool bigcell = len >= S2_BIG;
+        const uint32_t bigmask = __ballot_sync(FULL, bigcell && cmask != 0);
+        // long runs: super-tiles, starting at the one that holds the
+        // item's first query when it lies in the run (nearby in key order
+        // is mostly nearby in space) and alternating outwards
+        for (uint32_t bm = bigmask; bm; bm &= bm - 1) {
+            const int src = __ffs(bm) - 1;
+            const uint32_t cb = __shfl_sync(FULL, rb, src), ce = __shfl_sync(FULL, re, src);
+            const uint32_t cmk = __shfl_sync(FULL, cmask, src);
+            const int nst = (int)((ce - cb + S2_SUPER - 1) / S2_SUPER);
+            const uint32_t sq = qsv[0];
+            const int u0 = (a.self && sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
+            if constexpr (MEGA) {
+                // two cursors walk outwards from u0 (hi up, lo down),
+                // taking turns; entering a mega-tile, a cursor tests its
+                // box first and jumps over it when no query can use it
+                // (thresholds only fall, so a skipped group stays useless)
+                int hi = u0, lo = u0 - 1, mhi = -1, mlo = -1;
+                bool up = true;
+                while (hi < nst || lo >= 0) {
+                    int u;
+                    if (lo < 0 || (up && hi < nst)) {
+                        u = hi;
+                        const int M = u / S2_MEGA;
+                        if (M != mhi) {
+                            mhi = M;
+                            const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
+                            const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
+                            if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
+                                hi = (M + 1) * S2_MEGA;
+                                up = false;
+                                continue;
+                            }
+                        }
+                        ++hi;
+                    } else {
+                        u = lo;
+                        const int M = u / S2_MEGA;
+                        if (M != mlo) {
+                            mlo = M;
+                            const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
+                            const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
+                            if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
+                                lo = M * S2_MEGA - 1;
+                                up = true;
+                                continue;
+                            }
+                        }
+                        --lo;
+                    }
+                    up = !up;
+                    const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
+                    const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
+                    const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                    KNN_CNT(7, 1);
+                    if (!smask) continue;
+                    KNN_CNT(6, 1);
+                    if (DIM >= S2_WIDE_DIM) {
+                        // two tiles per step, as for the flattened runs
+                        for (uint32_t t0 = sb; t0 < se; t0 += 64) {
+                            const bool vA = t0 + lane < se, vB = t0 + 32 + lane < se;
+                            const uint32_t sA = vA ? t0 + lane : 0u, sB = vB ? t0 + 32 + lane : 0u;
+                            float cA[DIM], cB[DIM];
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
+                            if (vA) load_point<DIM>(a.xsort, sA, cA);
+                            if (vB) load_point<DIM>(a.xsort, sB, cB);
+                            st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
+                            KNN_ITEM_TILE(__popc(smask) * 2);
+                            scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
+                        }
+                    } else {
+                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
+                    }
+                }
+            } else {
+                // super-tiles alternating outwards from u0, one tile per step
+                for (int j = 0, left = nst; left > 0; ++j) {
+                    const int u = (j & 1) ? u0 + (j + 1) / 2 : u0 - j / 2;
+                    if (u < 0 || u >= nst) continue;
+                    --left;
+                    const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
+                    const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
+                    const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
+                    if (!smask) continue;
+                    scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
+                }
+            }
+        }
+        // (cells that no query of the item can use stay out of the
+        // flattened list)
+        const uint32_t flen = (bigcell || cmask == 0) ? 0u : len;
+        uint32_t inc = flen;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, inc, d);
+            if (lane >= d) inc += y;
+        }
+        const uint32_t exc = inc - flen;
+        const uint32_t total = __shfl_sync(FULL, inc, 31);
+        KNN_CNT(5, total);
+        KNN_PT(1);
+        // flattened position t -> (sorted position, cell's query mask)
+        auto locate = [&](uint32_t t, bool valid, uint32_t &sp, uint32_t &cmo) {
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                uint32_t ex = __shfl_sync(FULL, exc, src + step);
+                if (ex <= t) src += step;
+            }
+            const uint32_t sb = __shfl_sync(FULL, rb, src);
+            const uint32_t se = __shfl_sync(FULL, exc, src);
+            sp = valid ? sb + (t - se) : 0u;
+            const uint32_t cm = __shfl_sync(FULL, cmask, src);  // every lane takes part
+            cmo = valid ? cm : 0u;
+        };
+        if (DIM >= S2_WIDE_DIM) {
+            for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+                KNN_CYC_BEGIN(stp);
+                const bool vA = t0 + lane < total, vB = t0 + 32 + lane < total;
+                uint32_t sA, sB, cmA, cmB;
+                locate(t0 + lane, vA, sA, cmA);
+                locate(t0 + 32 + lane, vB, sB, cmB);
+                const uint32_t tmask = __reduce_or_sync(FULL, cmA | cmB);
+                KNN_CNT(0, 1);
+                KNN_CNT(1, __popc(tmask));
+                KNN_CNT(2, tmask == 0);
+                // lanes past the end get NaN coordinates: every distance
+                // comparison with them is false
+                float cA[DIM], cB[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
+                if (vA && KNN_GUARD(sA < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sA, cA);
+                if (vB && KNN_GUARD(sB < (uint64_t)a.n, 2)) load_point<DIM>(a.xsort, sB, cB);
+                st_cand += (unsigned long long)__popc(tmask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
+                KNN_ITEM_TILE(__popc(tmask) * 2);
+                KNN_CYC_END(stp, 8);
+                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
+            }
+        } else {
+            for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                const bool valid = t0 + lane < total;
+                uint32_t s, cmo;
+                locate(t0 + lane, valid, s, cmo);
+                const uint32_t tmask = __reduce_or_sync(FULL, cmo);
+                float c[DIM];
+                if (valid) {
+                    load_point<DIM>(a.xsort, s, c);
+                    st_cand += (unsigned long long)__popc(tmask);  // distances evaluated
+                    KNN_ITEM_TILE(__popc(tmask));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                }
+                scan2_tile<DIM, E>(c, s, valid, tmask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
+            }
+        }
+        KNN_PT(2);
+    }
+    __syncwarp();
+
+    if (lane < Q) cnt[lane] = my_cnt;
+    __syncwarp();
+
+    // a9 - a11, one query at a time, whole warp
+    for (int i = 0; i < Q; ++i) {
+        const int c0 = cnt[i];
+        uint32_t flag = 1;
+        if (c0 < 0) {
+            flag = 2;
+        } else if (c0 >= K) {
+            const uint64_t *bi = buf + i * BS;
+            // whole buffer in registers (blocked: entry g = lane*E + e) as
+            // 32-bit words: the FP32 key with its low bits replaced by the
+            // buffer slot.  Sorted, entry K-1 bounds T32 from above by at
+            // most the dropped bits, and the band (a prefix) stays a
+            // superset of every entry within T32 (1 + 2^-15) + 2^-120.
+            constexpr uint32_t SLOT = (uint32_t)B - 1;
+            // this lane's own (unsorted) entries g = lane*E + e: their FP32
+            // keys, and -- issued now, so that the sort below hides the
+            // latency -- the coordinates and original ids of their points
+            constexpr bool PREFETCH = E * (DIM + 1) <= 28;
+            uint32_t v[E], kr[E], sp[E];
+            float pc[PREFETCH ? E : 1][DIM];
+            uint32_t pid[PREFETCH ? E : 1];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int g = lane * E + e;
+                const uint64_t ent = g < c0 ? bi[g] : ~0ull;
+                kr[e] = (uint32_t)(ent >> 32) & ~SLOT;
+                sp[e] = (uint32_t)ent;
+                v[e] = g < c0 ? (kr[e] | (uint32_t)g) : 0xffffffffu;
+                if constexpr (PREFETCH) {
+                    const bool ok = g < c0 && KNN_GUARD(sp[e] < (uint64_t)a.n, 7);
+                    if (ok) {
+                        load_point<DIM>(a.xsort, sp[e], pc[e]);
+                        pid[e] = __ldg(&a.perm[sp[e]]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) pc[e][k] = 0.0f;
+                        pid[e] = 0;
+                    }
+                }
+            }
+            warp_bitonic_u32<E>(v, lane);
+            KNN_PT(3);
+            uint32_t vk = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e == (K - 1) % E) vk = v[e];
+            vk = __shfl_sync(FULL, vk, (K - 1) / E);
+            const uint32_t tb = __float_as_uint(band_thr(vk | SLOT)) & ~SLOT;
+            int mine = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) mine += (lane * E + e < c0 && (v[e] & ~SLOT) <= tb) ? 1 : 0;
+            int m = mine;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(FULL, m, o);
+            KNN_PT(4);
+            // exact canonical distances and original ids of the band: each
+            // lane scores its own unsorted entries that lie in the band (the
+            // band is the set of keys <= tb, the same test as above) and
+            // parks them by buffer slot -- D over the buffer entry, the id in
+            // the histogram area -- where the sorted positions pick them up
+            float q[DIM];
+            int32_t qi[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                q[k] = qc[i * QP + k];
+                qi[k] = a.fixed_ok ? to_fixed(q[k], a.F) : 0;
+            }
+            uint64_t *bw = buf + i * BS;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int g = lane * E + e;
+                if (g < c0 && kr[e] <= tb) {
+                    float c[DIM];
+                    uint32_t id;
+                    if constexpr (PREFETCH) {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) c[k] = pc[e][k];
+                        id = pid[e];
+                    } else {
+                        if (KNN_GUARD(sp[e] < (uint64_t)a.n, 7)) {
+                            load_point<DIM>(a.xsort, sp[e], c);
+                            id = a.perm[sp[e]];
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) c[k] = 0.0f;
+                            id = 0;
+                        }
+                    }
+                    uint64_t bits = 0;
+                    bool done = false;
+                    if (a.fixed_ok) {
+                        done = fsc != 0.0f && canon_d2_fixed_f32<DIM>(q, c, fsc, a.F, bits);
+                        if (!done) {
+                            int32_t ci[DIM];
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) ci[k] = to_fixed(c[k], a.F);
+                            done = canon_d2_fixed<DIM>(qi, ci, a.F, bits);
+                        }
+                    }
+                    if (!done) bits = canon_d2_fp64<DIM>(q, c);
+                    bw[g] = bits;
+                    hist[g] = id;
+                }
+            }
+            __syncwarp();
+            uint64_t D[E];
+            uint32_t I[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int g = lane * E + e;
+                D[e] = ~0ull;
+                I[e] = ~0u;
+                if (g < m) {
+                    const uint32_t slot = v[e] & SLOT;
+                    D[e] = bw[slot];
+                    I[e] = hist[slot];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) st_band += (unsigned long long)m;
+            KNN_CNT(12, c0);
+            KNN_CNT(13, m);
+            KNN_PT(5);
+            // the FP32 order is the exact order unless two near-equal
+            // values swap; check neighbours, re-sort by (D, id) if needed
+            bool inv = false;
+#pragma unroll
+            for (int e = 0; e + 1 < E; ++e)
+                inv = inv || (lane * E + e + 1 < m && xless(D[e + 1], I[e + 1], D[e], I[e]));
+            const uint64_t nd = __shfl_down_sync(FULL, D[0], 1);
+            const uint32_t ni = __shfl_down_sync(FULL, I[0], 1);
+            inv = inv || (lane < 31 && (lane + 1) * E < m && xless(nd, ni, D[E - 1], I[E - 1]));
+            if (__any_sync(FULL, inv)) {
+                KNN_CNT(14, 1);
+                warp_bitonic<E>(D, I, lane);
+            }
+            uint64_t dk = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e == (K - 1) % E) dk = D[e];
+            dk = __shfl_sync(FULL, dk, (K - 1) / E);
+            const float R = rcert[i];
+            bool certified = isinf(R);
+            if (!certified) {
+                const float R2 = __fmul_rd(__fmul_rd(R, R), 1.0f - 0x1p-20f);
+                certified = dk < f32_to_f64_bits_floor(R2);
+            }
+            KNN_PT(6);
+            // not certified: the K-th value bounds the next pass's threshold
+            if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
+            if (certified) {
+                flag = 0;
+                const int64_t rowq = (int64_t)a.qperm[qsv[i]] - a.row0;
+                const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
+                const bool rowok = KNN_GUARD(rowin, 5) && rowin;
+                const int64_t row = rowq * K;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int g = lane * E + e;
+                    if (g < K && rowok) {
+                        a.out_ids[row + g] = (int32_t)I[e];
+                        a.out_dist[row + g] = __longlong_as_double((long long)D[e]);  // D; k_sqrt_rows converts
+                    }
+                }
+            }
+        }
+        if (lane == 0) a.fail[qsv[i]] = flag;
+        KNN_PT(7);
+    }
+    __syncwarp();
+    KNN_ITEM_END(Q);
+}
+
+// The scan of one join: warps take work items from the join's queue.
+template <int DIM, int QM, int E, bool MEGA>
+__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(const __grid_constant__ ScanArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Scan2Warp<DIM, QM, E> w(smem + warp * scan2_warp_bytes(DIM, QM, E));
+    unsigned long long st_cand = 0, st_band = 0;
+    const float fsc = scan2_fixed_scale(a);
+    KNN_PT_DECL;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= a.nitems) break;
+        scan2_item<DIM, QM, E, MEGA>(a, item, w, lane, fsc, st_cand, st_band KNN_CNT_ARG);
+    }
+    KNN_PT_FLUSH;
+    scan2_flush_stats(a, st_cand, st_band, lane);
+}
+
+// The scan of several joins in one launch (batched joins): the work items of
+// all of them form one queue, ordered dense first across joins (entry = job
+// << 24 | item), and the joins' arguments sit in the launch's parameter space
+// (indexed by job; a warp reads the arguments of the job it works on).
+template <int DIM, int QM, int E, bool MEGA>
+__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2_multi(const __grid_constant__ MultiScanArgs p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Scan2Warp<DIM, QM, E> w(smem + warp * scan2_warp_bytes(DIM, QM, E));
+    unsigned long long st_cand = 0, st_band = 0;
+    int cur = -1;
+    KNN_PT_DECL;
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(p.counter, 1u);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= p.nuitems) break;
+        const uint32_t e = p.uitems[u];
+        const int job = (int)(e >> 24);
+        if (job != cur) {
+            if (cur >= 0) scan2_flush_stats(p.jobs[cur], st_cand, st_band, lane);
+            st_cand = st_band = 0;
+            cur = job;
+        }
+        const ScanArgs &a = p.jobs[job];
+        scan2_item<DIM, QM, E, MEGA>(a, e & 0xffffffu, w, lane, scan2_fixed_scale(a), st_cand, st_band KNN_CNT_ARG);
+    }
+    KNN_PT_FLUSH;
+    if (cur >= 0) scan2_flush_stats(p.jobs[cur], st_cand, st_band, lane);
+}
+
 
 }  // namespace knn

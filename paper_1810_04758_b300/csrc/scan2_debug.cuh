@@ -3,7 +3,9 @@
 // Built with -DKNN_PHASE_TIMING, lane 0 of every warp adds clock64() deltas
 // per phase of the scan kernel to g_phase and per-warp event counts to
 // g_count (read back and cleared by knnjoin_debug_phases); otherwise every
-// marker compiles to nothing and the kernel is unchanged.
+// marker compiles to nothing and the kernel is unchanged.  The state lives in
+// a DebugState that the kernel declares (KNN_PT_DECL) and hands to the
+// functions it calls (KNN_CNT_PARAM / KNN_CNT_ARG).
 #pragma once
 
 #ifdef KNN_PHASE_TIMING
@@ -14,34 +16,38 @@ namespace knn {
 __device__ unsigned long long g_phase[16];
 // g_count: event counts (meaning set by the KNN_CNT sites of the kernel).
 __device__ unsigned long long g_count[16];
+struct DebugState {
+    unsigned long long ph[8], pt, cn[16];
+};
 }  // namespace knn
-#define KNN_PT_DECL                                                      \
-    unsigned long long ph_[8] = {0, 0, 0, 0, 0, 0, 0, 0}, pt_ = clock64(); \
-    unsigned long long cn_[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}
+#define KNN_PT_DECL                          \
+    ::knn::DebugState dbg_;                  \
+    for (int q_ = 0; q_ < 8; ++q_) dbg_.ph[q_] = 0; \
+    for (int q_ = 0; q_ < 16; ++q_) dbg_.cn[q_] = 0; \
+    dbg_.pt = clock64()
 #define KNN_PT(i)                          \
     do {                                   \
         unsigned long long t_ = clock64(); \
-        ph_[i] += t_ - pt_;                \
-        pt_ = t_;                          \
+        dbg_.ph[i] += t_ - dbg_.pt;        \
+        dbg_.pt = t_;                      \
     } while (0)
-#define KNN_CNT(i, v)                        \
-    do {                                     \
-        cn_[i] += (unsigned long long)(v);   \
+#define KNN_CNT(i, v)                            \
+    do {                                         \
+        dbg_.cn[i] += (unsigned long long)(v);   \
     } while (0)
-// cycles of a stretch of code added to event count i (the stretch's clock
-// reads stay in place: volatile)
+// cycles of a stretch of code added to event count i
 #define KNN_CYC_BEGIN(nm) const unsigned long long nm##_c0 = clock64()
 #define KNN_CYC_END(nm, i) KNN_CNT(i, clock64() - nm##_c0)
-// extra parameter / argument that hands the counters to helper functions
-#define KNN_CNT_PARAM , unsigned long long *cn_
-#define KNN_CNT_ARG , cn_
-#define KNN_PT_FLUSH                                                      \
-    do {                                                                  \
-        if ((threadIdx.x & 31) == 0) {                                    \
-            for (int q_ = 0; q_ < 8; ++q_) atomicAdd(&g_phase[q_], ph_[q_]); \
-            for (int q_ = 0; q_ < 16; ++q_)                               \
-                if (cn_[q_]) atomicAdd(&g_count[q_], cn_[q_]);            \
-        }                                                                 \
+// extra parameter / argument that hands the state to called functions
+#define KNN_CNT_PARAM , ::knn::DebugState &dbg_
+#define KNN_CNT_ARG , dbg_
+#define KNN_PT_FLUSH                                                          \
+    do {                                                                      \
+        if ((threadIdx.x & 31) == 0) {                                        \
+            for (int q_ = 0; q_ < 8; ++q_) atomicAdd(&g_phase[q_], dbg_.ph[q_]); \
+            for (int q_ = 0; q_ < 16; ++q_)                                   \
+                if (dbg_.cn[q_]) atomicAdd(&g_count[q_], dbg_.cn[q_]);        \
+        }                                                                     \
     } while (0)
 #define KNN_ITEM_BEGIN unsigned long long it0_ = clock64(), itq_ = 0
 #define KNN_ITEM_TILE(x) itq_ += (x)

@@ -84,9 +84,39 @@ cudaError_t launch_one(const ScanArgs &a, size_t smem, cudaStream_t s, int nsm, 
     return cudaGetLastError();
 }
 
+template <int E, bool MEGA>
+cudaError_t launch_multi(const MultiScanArgs &p, size_t smem, cudaStream_t s, int nsm, int dev, bool *nofit,
+                         int64_t *launches)
+{
+    constexpr int QM = scan2_queries_per_item(E);
+    static bool configured[64] = {};
+    cudaError_t e = ensure_nb_order(dev);
+    if (e != cudaSuccess) return e;
+    if (!configured[dev & 63]) {
+        e = cudaFuncSetAttribute(k_scan2_multi<DIM, QM, E, MEGA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured[dev & 63] = true;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan2_multi<DIM, QM, E, MEGA>, S2_CTA, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) {
+        *nofit = true;
+        return cudaSuccess;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>(((int64_t)p.nuitems + S2_WARPS - 1) / S2_WARPS,
+                                                      (int64_t)occ * nsm);
+    if (grid == 0) return cudaSuccess;
+    k_scan2_multi<DIM, QM, E, MEGA><<<grid, S2_CTA, smem, s>>>(p);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 }  // namespace KNN_S2_NS
 
 using KNN_S2_NS::DIM;
+using KNN_S2_NS::launch_multi;
 using KNN_S2_NS::launch_one;
 
 template <>
@@ -101,6 +131,22 @@ cudaError_t scan2_launch<DIM>(const ScanArgs &a, int E, bool mega, size_t smem, 
     case 9: return launch_one<4, true>(a, smem, s, nsm, dev, nofit, launches);
     case 16: return launch_one<8, false>(a, smem, s, nsm, dev, nofit, launches);
     case 17: return launch_one<8, true>(a, smem, s, nsm, dev, nofit, launches);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t scan2_launch_multi<DIM>(const MultiScanArgs &p, int E, bool mega, size_t smem, cudaStream_t s, int nsm,
+                                    int dev, bool *nofit, int64_t *launches)
+{
+    *nofit = false;
+    switch (E * 2 + (mega ? 1 : 0)) {
+    case 4: return launch_multi<2, false>(p, smem, s, nsm, dev, nofit, launches);
+    case 5: return launch_multi<2, true>(p, smem, s, nsm, dev, nofit, launches);
+    case 8: return launch_multi<4, false>(p, smem, s, nsm, dev, nofit, launches);
+    case 9: return launch_multi<4, true>(p, smem, s, nsm, dev, nofit, launches);
+    case 16: return launch_multi<8, false>(p, smem, s, nsm, dev, nofit, launches);
+    case 17: return launch_multi<8, true>(p, smem, s, nsm, dev, nofit, launches);
     default: return cudaErrorInvalidValue;
     }
 }

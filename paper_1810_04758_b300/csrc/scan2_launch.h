@@ -11,6 +11,7 @@
 namespace knn {
 
 struct ScanArgs;
+struct MultiScanArgs;
 
 // Warps per CTA of k_scan2 (each works alone on its own work items).
 constexpr int S2_WARPS = 4;
@@ -50,6 +51,12 @@ __host__ __device__ constexpr int scan2_queries_per_item(int E) { return E <= 2 
 template <int DIM>
 cudaError_t scan2_launch(const ScanArgs &a, int E, bool mega, size_t smem, cudaStream_t s, int nsm, int dev,
                          bool *nofit, int64_t *launches);
+
+// The same for several joins at once: one launch of k_scan2_multi over the
+// union queue in p (all jobs of dimension DIM and buffer size E).
+template <int DIM>
+cudaError_t scan2_launch_multi(const MultiScanArgs &p, int E, bool mega, size_t smem, cudaStream_t s, int nsm,
+                               int dev, bool *nofit, int64_t *launches);
 
 // Checked builds (KNN_CHECKS): the failed-check word of this unit's kernels
 // (0 otherwise); clear = reset it to 0 after reading.
