@@ -99,7 +99,14 @@ typedef struct {
                                  ordered dense first across joins (Sec. 4.5 work queue).
                                  0 = the worker pool runs whole joins concurrently.
                                  Results are identical either way */
-    int reserved[3];
+    int tail_queries;         /* tail strategy (Sec. 5.4): when at most this many queries are
+                                 left uncertified -- after an epoch of the paper's policy, or
+                                 after the second pass of the default one -- they are finished
+                                 in one pass over the whole grid (a box that contains every
+                                 point certifies every query) instead of further widening.
+                                 0 = max(1024, queries / 100); negative = never.  Results are
+                                 identical; the number of passes changes */
+    int reserved[2];
 } knnjoin_config;
 
 /* One self-join (batched and served calls). */

@@ -45,7 +45,7 @@ class KnnjoinConfig(ctypes.Structure):
                 ("tune_cache_path", ctypes.c_char_p), ("width_mult", ctypes.c_float),
                 ("workers", ctypes.c_int), ("policy", ctypes.c_int), ("out_chunk_mb", ctypes.c_int),
                 ("large_first", ctypes.c_int), ("batch_union", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("tail_queries", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class KnnjoinJob(ctypes.Structure):
@@ -284,7 +284,7 @@ class Context:
     def __init__(self, device: int = 0, stream=None, width_mult: float = 0.0,
                  max_jobs: int = 0, hbm_budget_bytes: int = 0, workers: int = 0,
                  tune_cache_path: Optional[str] = None, policy: int = 0, out_chunk_mb: int = 0,
-                 large_first: bool = False, batch_union: bool = False):
+                 large_first: bool = False, batch_union: bool = False, tail_queries: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -304,6 +304,7 @@ class Context:
         cfg.out_chunk_mb = out_chunk_mb
         cfg.large_first = 1 if large_first else 0
         cfg.batch_union = 1 if batch_union else 0
+        cfg.tail_queries = tail_queries
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None
         cfg.tune_cache_path = self._tune_path
         self._cfg = cfg

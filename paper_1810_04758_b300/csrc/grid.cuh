@@ -481,6 +481,13 @@ __global__ void k_status_summary(const uint32_t *__restrict__ list, const uint32
     }
 }
 
+// The queries of a list go to level `l` (the tail strategy: the whole grid).
+__global__ void k_set_levels(const uint32_t *__restrict__ list, int64_t m, uint32_t *__restrict__ lvl, uint32_t l)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x)
+        lvl[list[a]] = l;
+}
+
 // ---------------------------------------------------------------------------
 // a3 / a5
 // ---------------------------------------------------------------------------

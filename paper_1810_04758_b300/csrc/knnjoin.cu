@@ -273,6 +273,7 @@ struct Pipeline {
     TuneTable *tune = nullptr;
     float force_wm = 0.0f;         // > 0: this multiplier (autotuning runs)
     int policy = 0;                // knnjoin_config.policy
+    int tail_queries = 0;          // knnjoin_config.tail_queries
     size_t out_chunk_bytes = 0;    // knnjoin_config.out_chunk_mb (0: automatic)
     int64_t launches = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
@@ -814,6 +815,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         CK(cudaMemsetAsync(done, 0, sizeof(uint32_t) * nq, s));
     }
     float eps_mult = 1.0f;
+    // tail strategy (Sec. 5.4): at most `tail_limit` queries left -> one pass
+    // over the whole grid (level top_level: a box holding every point, which
+    // certifies every query)
+    const int64_t tail_limit = tail_queries < 0 ? -1
+                               : tail_queries > 0 ? (int64_t)tail_queries
+                                                  : std::max<int64_t>(1024, nq / 100);
+    bool tail_epoch = false;  // the paper's policy: this epoch is the tail pass
     for (int epoch = 0;; ++epoch) {
         // a3-a5
         trace_phase.reset(new NvtxRange("a3-a6 keys, sort, gather, start levels"));
@@ -869,7 +877,8 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         // start level of every query (sliding-window cell counts)
         uint32_t *lvl = sc.get<uint32_t>("lvl", nq);
         if (policy == 1) {
-            k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, 0u); ++launches;
+            k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, tail_epoch ? (uint32_t)hp.top_level : 0u);
+            ++launches;
         } else if (!self) {
             // R x S: every query starts at the search-distance width (queries in
             // sparse regions move up a level per pass until certified)
@@ -1062,7 +1071,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.qkeys = qkeys;
                 a.qperm = qperm;
                 a.self = self ? 1 : 0;
-                a.rcap = policy == 1 && epoch < 4096 ? hp.w0 : 0.0f;
+                a.rcap = policy == 1 && !tail_epoch && epoch < 4096 ? hp.w0 : 0.0f;
                 a.row0 = row0;
                 a.out_rows = chunked ? chunk_rows : nrows;
                 a.nq = nq;
@@ -1185,6 +1194,13 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 std::swap(active, active2);
                 m = next;
                 ++pass;
+                if (m > 0 && pass >= 2 && tail_limit >= 0 && m <= tail_limit) {
+                    // the tail: the rest in one pass over the whole grid
+                    k_set_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, m, lvl, (uint32_t)hp.top_level);
+                    ++launches;
+                    next_lmin = next_lmax = (uint32_t)hp.top_level;
+                    range_known = true;
+                }
             }
             if (chunked) {
                 const int64_t rows = r1 - r0;
@@ -1194,6 +1210,12 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             }
         }
         if (policy != 1 || m == 0) break;
+        if (!tail_epoch && tail_limit >= 0 && m <= tail_limit) {
+            // the rest in one pass over the whole grid of this epoch
+            tail_epoch = true;
+            continue;
+        }
+        tail_epoch = false;
         // re-index: eps += eps_min / 2 (doubling after 256 epochs)
         eps_mult = epoch < 256 ? eps_mult + 0.5f : eps_mult * 2.0f;
         pin.width_mult = eps_mult;
@@ -1459,6 +1481,7 @@ static void start_workers(knnjoin_ctx *ctx)
         w->pipe.width_mult = ctx->main.width_mult;
         w->pipe.tune = &ctx->tune;
         w->pipe.policy = ctx->main.policy;
+        w->pipe.tail_queries = ctx->main.tail_queries;
         w->pipe.out_chunk_bytes = ctx->main.out_chunk_bytes;
         ctx->workers.push_back(std::move(w));
     }
@@ -1498,6 +1521,7 @@ static void run_union_batch(knnjoin_ctx *ctx, const knnjoin_job *jobs, int njobs
         P->width_mult = ctx->main.width_mult;
         P->tune = &ctx->tune;
         P->policy = ctx->main.policy;
+        P->tail_queries = ctx->main.tail_queries;
         P->out_chunk_bytes = ctx->main.out_chunk_bytes;
         ctx->upipes.push_back(std::move(P));
     }
@@ -1620,6 +1644,7 @@ knnjoin_status knnjoin_create(const knnjoin_config *cfg, knnjoin_ctx **out)
         ctx->main.tune = &ctx->tune;
         if (ctx->cfg.policy < 0 || ctx->cfg.policy > 1) fail(KNN_ERR_INVALID, "policy must be 0 or 1");
         ctx->main.policy = ctx->cfg.policy;
+        ctx->main.tail_queries = ctx->cfg.tail_queries;
         if (ctx->cfg.out_chunk_mb < 0) fail(KNN_ERR_INVALID, "out_chunk_mb must be >= 0");
         ctx->main.out_chunk_bytes = (size_t)ctx->cfg.out_chunk_mb << 20;
         if (ctx->cfg.max_jobs > 0) ctx->max_jobs = ctx->cfg.max_jobs;
@@ -1739,6 +1764,7 @@ knnjoin_status knnjoin_index_create(knnjoin_ctx *ctx, const float *points, int64
         ix->pipe.init(ctx->device, ix->stream, &ctx->al);
         ix->pipe.width_mult = ctx->main.width_mult;
         ix->pipe.tune = &ctx->tune;
+        ix->pipe.tail_queries = ctx->main.tail_queries;
         // work queued on the context's stream (the points' producer) first
         CK(cudaEventRecord(ctx->main.ev[0], ctx->stream));
         CK(cudaStreamWaitEvent(ix->stream, ctx->main.ev[0], 0));

@@ -1,7 +1,10 @@
 """The paper's GPU-Only policy (knnjoin_config.policy = 1): one global eps,
 a query fails when fewer than K neighbours lie within eps, failed queries
 are redone on a grid re-indexed with eps += eps_min / 2.  Only the schedule
-differs from the default policy: rows must equal the oracle's."""
+differs from the default policy: rows must equal the oracle's.  The policy
+itself is tested with the tail strategy off; the tail strategy (Sec. 5.4:
+the last few queries in one pass over the whole grid) is tested beside it,
+under both policies."""
 import numpy as np
 import pytest
 
@@ -15,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def ctx():
     from paper_1810_04758_b300 import build, Context
     build.build()
-    c = Context(device=0, policy=1)
+    c = Context(device=0, policy=1, tail_queries=-1)
     yield c
     c.close()
 
@@ -62,3 +65,40 @@ def test_paper_policy_r_x_s(ctx):
     wi, wd = oracle.bf_rs(q, p, 16)
     np.testing.assert_array_equal(gi.cpu().numpy(), wi)
     np.testing.assert_array_equal(gd.cpu().numpy(), wd)
+
+
+@pytest.mark.parametrize("kind,d,n,K", [("expo", 3, 30000, 32), ("expo", 6, 12000, 32),
+                                        ("clustered2d", 2, 40000, 16)])
+def test_tail_strategy_paper_policy(kind, d, n, K):
+    import torch
+    from paper_1810_04758_b300 import Context
+    p = gen.make_points(kind, n, d, seed=75)
+    t = torch.from_numpy(p).cuda()
+    with Context(device=0, policy=1, tail_queries=-1) as off, Context(device=0, policy=1) as on:
+        io, do = off.self_join(t, K)
+        so = off.stats()
+        it, dt = on.self_join(t, K)
+        st = on.stats()
+    torch.cuda.synchronize()
+    assert torch.equal(io, it) and torch.equal(do, dt)
+    assert st["passes"] <= so["passes"]
+    wi, wd = oracle.bf(p, K)
+    np.testing.assert_array_equal(it.cpu().numpy(), wi)
+    np.testing.assert_array_equal(dt.cpu().numpy(), wd)
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_tail_strategy_forced(policy):
+    # every query left after the first epoch / second pass goes to the whole grid
+    import torch
+    from paper_1810_04758_b300 import Context
+    p = gen.make_points("expo", 25000, 4, seed=76)
+    t = torch.from_numpy(p).cuda()
+    with Context(device=0, policy=policy, tail_queries=1 << 30) as c:
+        ids, dist = c.self_join(t, 64)
+        st = c.stats()
+    torch.cuda.synchronize()
+    assert st["passes"] <= (2 if policy == 1 else 3)
+    wi, wd = oracle.bf(p, 64)
+    np.testing.assert_array_equal(ids.cpu().numpy(), wi)
+    np.testing.assert_array_equal(dist.cpu().numpy(), wd)
