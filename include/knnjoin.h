@@ -192,6 +192,29 @@ knnjoin_status knnjoin_join(knnjoin_ctx *ctx, const float *queries, int64_t nq, 
 knnjoin_status knnjoin_self_join_rows(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
                                       int64_t row_begin, int64_t row_end, int32_t *out_ids, double *out_dist);
 
+/* Cost-balanced shards of a self-join (the paper's multi-GPU note, Sec. 6:
+ * its density-ordered work queue split over a node's GPUs).  Equal row
+ * counts are unequal work when the input is spatially ordered or skewed, so
+ * the queries are taken in the index's key order (cells contiguous) and cut
+ * into nshards ranges of equal estimated cost: a query in a cell whose 3^d
+ * neighbourhood holds N points costs N (its candidates at ring 1, Alg. 1).
+ * knnjoin_shard_bounds: bounds int64 [nshards + 1] (host) receives the cut
+ *   points, sorted query positions 0 = bounds[0] <= ... <= bounds[nshards] =
+ *   n; costs double [nshards] (host, optional) each range's estimated cost.
+ *   Deterministic: every GPU computes the same bounds for the same points.
+ * knnjoin_self_join_range: the queries at sorted positions [pos_begin,
+ *   pos_end): out_rows int64 [m] (host or device) receives the original row
+ *   of each output row, out_ids / out_dist [m][K] (m = pos_end - pos_begin)
+ *   the rows of knnjoin_self_join for those points, bit for bit.
+ * Both require the default policy (knnjoin_config.policy = 0); otherwise as
+ * knnjoin_self_join, and 0 <= pos_begin < pos_end <= n, 1 <= nshards <=
+ * 4096, else KNN_ERR_INVALID. */
+knnjoin_status knnjoin_shard_bounds(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int nshards,
+                                    int64_t *bounds, double *costs);
+knnjoin_status knnjoin_self_join_range(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                       int64_t pos_begin, int64_t pos_end, int64_t *out_rows, int32_t *out_ids,
+                                       double *out_dist);
+
 /* Resident index: index a data set once and keep it on the device, then
  * answer R x S queries against it (the same result as knnjoin_join with these
  * points: for each query row the K nearest data rows under (D, j), nothing

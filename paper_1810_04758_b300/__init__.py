@@ -34,7 +34,8 @@ EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_jo
            "knnjoin_submit", "knnjoin_poll", "knnjoin_cancel", "knnjoin_get_stats",
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc",
            "knnjoin_fp32_mismatch", "knnjoin_index_create", "knnjoin_index_query",
-           "knnjoin_index_stats", "knnjoin_index_destroy", "knnjoin_self_join_rows")
+           "knnjoin_index_stats", "knnjoin_index_destroy", "knnjoin_self_join_rows",
+           "knnjoin_shard_bounds", "knnjoin_self_join_range")
 KNN_NOALLOC_MAX_POINTS = 65536
 
 
@@ -116,6 +117,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_fp32_mismatch.restype = I
     lib.knnjoin_self_join_rows.argtypes = [P, P, I64, I, I, I64, I64, P, P]
     lib.knnjoin_self_join_rows.restype = I
+    lib.knnjoin_shard_bounds.argtypes = [P, P, I64, I, I, I, P, P]
+    lib.knnjoin_shard_bounds.restype = I
+    lib.knnjoin_self_join_range.argtypes = [P, P, I64, I, I, I64, I64, P, P, P]
+    lib.knnjoin_self_join_range.restype = I
     lib.knnjoin_index_create.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.knnjoin_index_create.restype = I
     lib.knnjoin_index_query.argtypes = [P, P, I64, I, P, P]
@@ -202,6 +207,41 @@ def knnjoin_self_join_rows(ctx: int, points: int, n: int, d: int, K: int, row_be
                            out_ids: int, out_dist: int) -> int:
     return _check(ctx, load_library().knnjoin_self_join_rows(ctx, points, n, d, K, row_begin, row_end,
                                                              out_ids, out_dist))
+
+
+def knnjoin_shard_bounds(ctx: int, points: int, n: int, d: int, K: int, nshards: int):
+    """(bounds int64 [nshards + 1], costs float64 [nshards]) of the
+    cost-balanced shards (sorted query positions)."""
+    import numpy as np
+    bounds = np.zeros(nshards + 1, np.int64)
+    costs = np.zeros(nshards, np.float64)
+    _check(ctx, load_library().knnjoin_shard_bounds(ctx, points, n, d, K, nshards, bounds.ctypes.data,
+                                                    costs.ctypes.data))
+    return bounds, costs
+
+
+def knnjoin_self_join_range(ctx: int, points: int, n: int, d: int, K: int, pos_begin: int, pos_end: int,
+                            out_rows: int, out_ids: int, out_dist: int) -> int:
+    return _check(ctx, load_library().knnjoin_self_join_range(ctx, points, n, d, K, pos_begin, pos_end, out_rows,
+                                                              out_ids, out_dist))
+
+
+def gather_shards(n: int, K: int, parts):
+    """Reassemble a self-join's rows from shards given as (rows, ids, dist)
+    numpy arrays (rows: the original row of each shard row): ids int32 [n, K]
+    and dist float64 [n, K].  Every row must be covered exactly once."""
+    import numpy as np
+    ids = np.full((n, K), -1, np.int32)
+    dist = np.full((n, K), np.nan, np.float64)
+    seen = np.zeros(n, np.int64)
+    for rows, i, d in parts:
+        rows = np.asarray(rows, np.int64)
+        np.add.at(seen, rows, 1)
+        ids[rows] = i
+        dist[rows] = d
+    if not (seen == 1).all():
+        raise ValueError("shards do not cover every row exactly once")
+    return ids, dist
 
 
 def knnjoin_index_create(ctx: int, points: int, n: int, d: int, K: int) -> int:
@@ -365,6 +405,27 @@ class Context:
         knnjoin_self_join_rows(self.ctx, points.data_ptr(), n, d, K, row_begin, row_end, out_ids.data_ptr(),
                                out_dist.data_ptr())
         return out_ids, out_dist
+
+    def shard_bounds(self, points, K: int, nshards: int):
+        """Cost-balanced cut points (sorted query positions, int64 [nshards + 1])
+        and each shard's estimated cost."""
+        points = points.contiguous()
+        n, d = points.shape
+        return knnjoin_shard_bounds(self.ctx, points.data_ptr(), n, d, K, nshards)
+
+    def self_join_range(self, points, K: int, pos_begin: int, pos_end: int):
+        """The queries at sorted positions [pos_begin, pos_end) (one
+        cost-balanced shard): (rows int64 [m], ids int32 [m, K], dist float64
+        [m, K]), rows = the original row of each output row."""
+        torch = self._torch
+        points = points.contiguous()
+        n, d = points.shape
+        m = pos_end - pos_begin
+        rows = torch.empty(max(m, 1), dtype=torch.int64, device=points.device)
+        out_ids, out_dist = self._outputs(max(m, 1), K, points, None, None)
+        knnjoin_self_join_range(self.ctx, points.data_ptr(), n, d, K, pos_begin, pos_end, rows.data_ptr(),
+                                out_ids.data_ptr(), out_dist.data_ptr())
+        return rows, out_ids, out_dist
 
     def autotune(self, points, K: int) -> float:
         """Time the self-join of `points` at several cell-width multipliers and

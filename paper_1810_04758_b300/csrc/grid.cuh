@@ -713,6 +713,108 @@ __global__ void k_mark_done(const uint32_t *__restrict__ list, const uint32_t *_
 
 // Chunked or sharded output: flags[a] = (the original row of sorted query
 // position list[a] lies in [r0, r1)).
+// Sorted-position shard (cost-balanced shards): flags[a] = list[a] in [r0, r1).
+__global__ void k_pos_flags(const uint32_t *__restrict__ list, int64_t m, uint32_t r0, uint32_t r1,
+                            uint32_t *__restrict__ flags)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x)
+        flags[a] = list[a] >= r0 && list[a] < r1;
+}
+
+// Original rows of the sorted positions [p0, p0 + m) (int64).
+__global__ void k_rows_of(const uint32_t *__restrict__ perm, int64_t p0, int64_t m, int64_t *__restrict__ rows)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x)
+        rows[a] = perm[p0 + a];
+}
+
+// Shard cost model, per level: the points of each non-empty cell's 3^d
+// neighbourhood (Alg. 1, ring 1), cells found in the level's dense table or
+// hash map.
+__global__ void k_cell_around(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ begin,
+                              const uint32_t *ncells_p, int shift, int d, int nbits, DenseDims dims, DenseDims cmax,
+                              const uint2 *__restrict__ dense, const uint4 *__restrict__ hslot, uint32_t hmask,
+                              uint32_t *__restrict__ around)
+{
+    int noff = 1;
+    for (int k = 0; k < d; ++k) noff *= 3;
+    const uint32_t ncells = *ncells_p;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        int cell[MAX_DIM], nb[MAX_DIM];
+        morton_decode(keys[begin[c]] >> shift, d, nbits, cell);
+        uint32_t sum = 0;
+        for (int o = 0; o < noff; ++o) {
+            int r = o;
+            bool ok = true;
+            uint32_t idx = 0;
+            for (int k = 0; k < d; ++k) {
+                nb[k] = cell[k] + r % 3 - 1;
+                r /= 3;
+                ok = ok && nb[k] >= 0 && nb[k] <= (int)cmax.stride[k];
+                idx += (uint32_t)nb[k] * dims.stride[k];
+            }
+            if (!ok) continue;
+            const uint2 rg = dense ? dense[idx] : hash_lookup(hslot, hmask, morton_encode(nb, d, nbits));
+            sum += rg.y - rg.x;
+        }
+        around[c] = sum;
+    }
+}
+
+// Cell (run) index of every sorted position at a level: inclusive count of
+// run starts - 1.
+__global__ void k_run_index(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ rid, int64_t n,
+                            uint32_t *__restrict__ idx)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x)
+        idx[a] = rid[a] + flags[a] - 1u;
+}
+
+// Per-level arrays of the shard cost model, levels [lmin, lmax].
+constexpr int COST_MAX_LEVELS = 12;
+struct QueryCostArgs {
+    const uint32_t *idx[COST_MAX_LEVELS];     // cell index of each sorted position
+    const uint32_t *around[COST_MAX_LEVELS];  // neighbourhood points of each cell
+    int lmin, lmax;
+};
+
+// Cost of each query: the neighbourhood points at its start level, and at
+// the levels above while that count is below 2K (where it would fail and be
+// re-queued), as the candidates it is expected to evaluate.
+__global__ void k_query_costs(const uint32_t *__restrict__ lvl, int64_t n, int K, const QueryCostArgs c,
+                              float *__restrict__ cost)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        int l = max((int)lvl[s], c.lmin);
+        float sum = 0.0f;
+        for (; l <= c.lmax; ++l) {
+            const uint32_t a = c.around[l - c.lmin][c.idx[l - c.lmin][s]];
+            sum += (float)a;
+            if (a >= 2u * (uint32_t)K) break;
+        }
+        cost[s] = sum;
+    }
+}
+
+// Smallest and largest value of a uint32 array (out[0] min, out[1] max,
+// initialised to ~0 and 0).
+__global__ void k_minmax_u32(const uint32_t *__restrict__ v, int64_t n, uint32_t *out)
+{
+    uint32_t lo = 0xffffffffu, hi = 0;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x) {
+        lo = min(lo, v[a]);
+        hi = max(hi, v[a]);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+        hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&out[0], lo);
+        atomicMax(&out[1], hi);
+    }
+}
+
 __global__ void k_row_flags(const uint32_t *__restrict__ list, const uint32_t *__restrict__ qperm, int64_t m,
                             uint32_t r0, uint32_t r1, uint32_t *__restrict__ flags)
 {

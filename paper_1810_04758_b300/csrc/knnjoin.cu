@@ -290,6 +290,11 @@ struct Pipeline {
     // parameters and, as they are built, the level hash maps; res_mode 2
     // makes run() answer R x S queries against what was kept
     int res_mode = 0;
+    // cost-balanced shards: run() computes sorted query positions [row_b,
+    // row_e) (output row = position - row_b) and writes the original row of
+    // each output row to shard_rows_out (int64, host or device)
+    bool shard_sorted = false;
+    int64_t *shard_rows_out = nullptr;
     // batched joins scanned together: the scan of each pass goes through this
     // coordinator (one launch over the work items of every join of the batch)
     struct UnionScan *uscan = nullptr;
@@ -394,6 +399,35 @@ struct Pipeline {
     // (row_e < 0: all) are computed, into outputs of row_e - row_b rows
     void run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in, double *dist_in,
              const float *qry_in = nullptr, int64_t nq_in = 0, int64_t row_b = 0, int64_t row_e = -1);
+
+    // start level of every sorted position of a self-join (sliding-window
+    // cell counts over the sorted keys)
+    void start_levels(const uint64_t *keys, int64_t n, int d, int K, float wmul, const GridParams &hp,
+                      uint32_t *lvl)
+    {
+        // target count of a query's parent cell: between the expected counts
+        // of the ideal level's parent and of the ideal level itself
+        const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
+        const double ideal = std::pow(2.0 * (double)wmul, d) * (double)K / Vd;
+        int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
+        if (hp.finer == 0) {
+            // no density skew: every query starts at the search-distance width
+            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.start_level); ++launches;
+        } else if (n >= H && hp.top_level > 0) {
+            const int64_t nw = n - H + 1;
+            uint8_t *pm = sc.get<uint8_t>("win_pm", nw), *smn = sc.get<uint8_t>("win_sm", nw);
+            const int64_t nblk = (nw + H - 1) / H;
+            k_window_blocks<<<grid_for(nblk, 128, nsm, 16), 128, 0, s>>>(keys, nw, H, d, pm, smn); ++launches;
+            k_start_levels<<<grid_for(n, 256, nsm), 256, 0, s>>>(pm, smn, n, H, hp.top_level, hp.start_level, lvl);
+            ++launches;
+        } else {
+            k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.top_level); ++launches;
+        }
+    }
+
+    // cut points of nshards cost-balanced ranges of sorted query positions
+    // (bounds[0] = 0 .. bounds[nshards] = n) and each range's estimated cost
+    void shard_bounds(const float *pts, int64_t n, int d, int K, int nshards, int64_t *bounds, double *costs);
 };
 
 __global__ void k_init_reduce(PrepReduce *r)
@@ -666,7 +700,9 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     const int rmode = res_mode;           // 1: build a resident index, 2: query one
     if (row_e < 0) row_e = nq;
     const int64_t nrows = row_e - row_b;  // output rows (a shard of the queries, or all)
-    const bool sharded = nrows < nq;
+    const bool sharded = nrows < nq || shard_sorted;
+    if (shard_sorted && (!self || policy != 0 || rmode != 0))
+        fail(KNN_ERR_INVALID, "cost-balanced shards: self-joins under the default policy only");
     CK(cudaSetDevice(device));
     const bool pts_dev = device_side(pts_in, device, "points");
     const bool ids_dev = device_side(ids_in, device, "out_ids");
@@ -702,7 +738,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // exceed out_chunk_bytes) are computed in chunks of query rows, each
     // copied out before the next
     int64_t chunk_rows = nrows;
-    if (policy == 0 && rmode != 1 && !(ids_dev && dist_dev)) {
+    if (policy == 0 && rmode != 1 && !(ids_dev && dist_dev) && !shard_sorted) {
         const size_t row_bytes = (size_t)K * (sizeof(int32_t) + sizeof(double));
         size_t limit = out_chunk_bytes;
         if (limit == 0) {
@@ -822,6 +858,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                                : tail_queries > 0 ? (int64_t)tail_queries
                                                   : std::max<int64_t>(1024, nq / 100);
     bool tail_epoch = false;  // the paper's policy: this epoch is the tail pass
+    uint32_t *last_perm = nullptr;  // the last epoch's sorted -> original map
     for (int epoch = 0;; ++epoch) {
         // a3-a5
         trace_phase.reset(new NvtxRange("a3-a6 keys, sort, gather, start levels"));
@@ -838,6 +875,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             xsort = sc.get<float>("xsort", (size_t)n * pad_dim(d));
             k_gather<<<grid_for(n, 256, nsm), 256, 0, s>>>(xs, n, d, perm, xsort); ++launches;
         }
+        last_perm = perm;
         if (rmode == 1) {
             // resident index built: keep the data side and stop (no queries)
             CK(cudaGetLastError());
@@ -884,23 +922,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             // sparse regions move up a level per pass until certified)
             k_fill_u32<<<grid_for(nq, 256, nsm), 256, 0, s>>>(lvl, nq, hp.start_level); ++launches;
         } else {
-            // target count of a query's parent cell: between the expected counts
-            // of the ideal level's parent and of the ideal level itself
-            const double Vd = std::pow(M_PI, d / 2.0) / std::tgamma(d / 2.0 + 1.0);
-            const double ideal = std::pow(2.0 * (double)wmul, d) * (double)K / Vd;
-            int64_t H = (int64_t)std::max(2.0, std::floor(ideal / std::pow(2.0, d / 2.0)));
-            if (hp.finer == 0) {
-                // no density skew: every query starts at the search-distance width
-                k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.start_level); ++launches;
-            } else if (n >= H && hp.top_level > 0) {
-                const int64_t nw = n - H + 1;
-                uint8_t *pm = sc.get<uint8_t>("win_pm", nw), *smn = sc.get<uint8_t>("win_sm", nw);
-                const int64_t nblk = (nw + H - 1) / H;
-                k_window_blocks<<<grid_for(nblk, 128, nsm, 16), 128, 0, s>>>(keys, nw, H, d, pm, smn); ++launches;
-                k_start_levels<<<grid_for(n, 256, nsm), 256, 0, s>>>(pm, smn, n, H, hp.top_level, hp.start_level, lvl); ++launches;
-            } else {
-                k_fill_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, hp.top_level); ++launches;
-            }
+            start_levels(keys, n, d, K, wmul, hp, lvl);
         }
 
         // pass loop
@@ -1022,7 +1044,12 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             if ((chunked || sharded) && m > 0) {
                 // this chunk's queries: the entries of the active list (all
                 // queries, or those not done yet) whose original row is in [r0, r1)
-                k_row_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, qperm, m, (uint32_t)r0, (uint32_t)r1, flags); ++launches;
+                if (shard_sorted) {
+                    k_pos_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, m, (uint32_t)r0, (uint32_t)r1, flags);
+                } else {
+                    k_row_flags<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, qperm, m, (uint32_t)r0, (uint32_t)r1, flags);
+                }
+                ++launches;
                 scan(flags, rid, m);
                 fetch(pinned, rid + m - 1, 4);
                 fetch(pinned + 1, flags + m - 1, 4);
@@ -1073,6 +1100,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.self = self ? 1 : 0;
                 a.rcap = policy == 1 && !tail_epoch && epoch < 4096 ? hp.w0 : 0.0f;
                 a.row0 = row0;
+                a.sorted_rows = shard_sorted ? 1 : 0;
                 a.out_rows = chunked ? chunk_rows : nrows;
                 a.nq = nq;
                 a.counter = small + 3;
@@ -1228,6 +1256,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     if (!chunked) {
         k_sqrt_rows<<<grid_for(nrows * K, 256, nsm, 16), 256, 0, s>>>(dist, nrows * K); ++launches;
     }
+    if (shard_sorted && shard_rows_out) {
+        // the original row of each output row (sorted position row_b + j)
+        const bool rows_dev = device_side(shard_rows_out, device, "out_rows");
+        int64_t *rows = rows_dev ? shard_rows_out : sc.get<int64_t>("shard_rows", (size_t)nrows);
+        k_rows_of<<<grid_for(nrows, 256, nsm), 256, 0, s>>>(last_perm, row_b, nrows, rows);
+        ++launches;
+        if (!rows_dev) CK(cudaMemcpyAsync(shard_rows_out, rows, sizeof(int64_t) * nrows, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaEventRecord(ev[2], s));
     if (turn.owns_lock()) {
         CK(cudaEventSynchronize(ev[2]));
@@ -1260,6 +1296,102 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     stats.ms_index = ms1;
     stats.ms_scan = ms_scan;
     stats.launches = launches;
+}
+
+// Cost-balanced shards (Sec. 6, one join split over GPUs).  Queries are
+// taken in the index's key order (cells contiguous, neighbouring cells
+// mostly nearby).  A query costs the points of its 3^d neighbourhood at its
+// start level (the join's own, from the sliding-window cell counts: sparse
+// regions start coarser) -- the candidates it evaluates at ring 1 -- plus
+// those one and two levels up while that count is below 2K, where it will
+// not be certified and is re-queued.  The cut points split the total cost
+// evenly between queries.
+void Pipeline::shard_bounds(const float *pts, int64_t n, int d, int K, int nshards, int64_t *bounds, double *costs)
+{
+    // the data's index (steps a1-a5), kept as a resident index would be
+    const int saved_mode = res_mode;
+    res_mode = 1;
+    try {
+        run(pts, n, d, K, nullptr, nullptr);
+    } catch (...) {
+        res_mode = saved_mode;
+        throw;
+    }
+    res_mode = saved_mode;
+    const GridParams hp = res_hp;
+    // the join's own start levels of the queries
+    uint32_t *lvl = sc.get<uint32_t>("lvl", n), *small = sc.get<uint32_t>("small", 16);
+    start_levels(res_keys, n, d, K, res_wm, hp, lvl);
+    k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
+    k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
+    k_minmax_u32<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, small + 4); ++launches;
+    fetch(pinned, small + 4, 8);
+    CK(cudaStreamSynchronize(s));
+    QueryCostArgs qa;
+    memset(&qa, 0, sizeof(qa));
+    qa.lmin = (int)pinned[0];
+    qa.lmax = std::min(std::min(hp.top_level, (int)pinned[1] + 2), qa.lmin + COST_MAX_LEVELS - 1);
+    // per level: cells, their table, each cell's neighbourhood points, and the
+    // cell of every sorted position
+    uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
+    uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1);
+    for (int l = qa.lmin; l <= qa.lmax; ++l) {
+        const int j = l - qa.lmin, sh = d * l;
+        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(res_keys, nullptr, n, sh, flags); ++launches;
+        scan(flags, rid, n);
+        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
+        uint32_t *idx = sc.get<uint32_t>("shard_idx" + std::to_string(j), n);
+        k_run_index<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, idx); ++launches;
+        const uint32_t nc = read1(small + 0);
+        DenseDims dd{}, cm{};
+        double G = 1.0;
+        for (int k = 0; k < d; ++k) {
+            dd.stride[k] = (uint32_t)G;
+            cm.stride[k] = (uint32_t)(hp.cmax0[k] >> l);
+            G *= (double)(cm.stride[k] + 1);
+        }
+        uint2 *dense = nullptr;
+        uint4 *slot = nullptr;
+        uint32_t hmask = 0;
+        if (G <= std::max(2.0 * (double)n, 65536.0)) {
+            dense = sc.get<uint2>("shard_dense", (size_t)G);
+            CK(cudaMemsetAsync(dense, 0, sizeof(uint2) * (size_t)G, s));
+            k_dense_insert<<<grid_for(n, 256, nsm), 256, 0, s>>>(res_keys, cbegin, small + 0, sh, d, hp.bits - l, dd,
+                                                                  dense); ++launches;
+        } else {
+            uint32_t H = 1;
+            while (H < 2 * nc) H <<= 1;
+            slot = sc.get<uint4>("shard_hslot", H);
+            CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
+            k_hash_insert<<<grid_for(nc, 256, nsm), 256, 0, s>>>(res_keys, cbegin, small + 0, sh, slot, H - 1);
+            ++launches;
+            hmask = H - 1;
+        }
+        uint32_t *around = sc.get<uint32_t>("shard_around" + std::to_string(j), nc);
+        k_cell_around<<<grid_for(nc, 256, nsm), 256, 0, s>>>(res_keys, cbegin, small + 0, sh, d, hp.bits - l, dd, cm,
+                                                              dense, slot, hmask, around); ++launches;
+        qa.idx[j] = idx;
+        qa.around[j] = around;
+    }
+    float *qcost = sc.get<float>("shard_qcost", n);
+    k_query_costs<<<grid_for(n, 256, nsm), 256, 0, s>>>(lvl, n, K, qa, qcost); ++launches;
+    CK(cudaGetLastError());
+    std::vector<float> hq(n);
+    CK(cudaMemcpyAsync(hq.data(), qcost, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // equal shares of the total cost, cut between queries
+    std::vector<double> cum(n + 1, 0.0);
+    for (int64_t q = 0; q < n; ++q) cum[q + 1] = cum[q] + (double)hq[q];
+    const double total = cum[n];
+    bounds[0] = 0;
+    bounds[nshards] = n;
+    for (int sh = 1; sh < nshards; ++sh) {
+        const double target = total * (double)sh / (double)nshards;
+        const int64_t p = (int64_t)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+        bounds[sh] = std::max<int64_t>(bounds[sh - 1], std::min<int64_t>(p, n));
+    }
+    if (costs)
+        for (int sh = 0; sh < nshards; ++sh) costs[sh] = cum[bounds[sh + 1]] - cum[bounds[sh]];
 }
 
 void validate_sizes(int64_t n, int d, int K);
@@ -1732,6 +1864,49 @@ knnjoin_status knnjoin_self_join_rows(knnjoin_ctx *ctx, const float *points, int
         if (row_begin < 0 || row_begin >= row_end || row_end > n)
             fail(KNN_ERR_INVALID, "rows must satisfy 0 <= row_begin < row_end <= n");
         ctx->main.run(points, n, d, K, out_ids, out_dist, nullptr, 0, row_begin, row_end);
+    });
+}
+
+knnjoin_status knnjoin_shard_bounds(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int nshards,
+                                    int64_t *bounds, double *costs)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!points || !bounds) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        if (nshards < 1 || nshards > 4096) fail(KNN_ERR_INVALID, "nshards must be in [1, 4096]");
+        if (ctx->main.policy != 0) fail(KNN_ERR_INVALID, "cost-balanced shards need the default policy");
+        std::vector<int64_t> b(nshards + 1);
+        std::vector<double> cs(nshards);
+        ctx->main.shard_bounds(points, n, d, K, nshards, b.data(), cs.data());
+        memcpy(bounds, b.data(), sizeof(int64_t) * (nshards + 1));
+        if (costs) memcpy(costs, cs.data(), sizeof(double) * nshards);
+    });
+}
+
+knnjoin_status knnjoin_self_join_range(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
+                                       int64_t pos_begin, int64_t pos_end, int64_t *out_rows, int32_t *out_ids,
+                                       double *out_dist)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        validate(points, n, d, K, out_ids, out_dist);
+        if (!out_rows) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        if (pos_begin < 0 || pos_begin >= pos_end || pos_end > n)
+            fail(KNN_ERR_INVALID, "positions must satisfy 0 <= pos_begin < pos_end <= n");
+        if (ctx->main.policy != 0) fail(KNN_ERR_INVALID, "cost-balanced shards need the default policy");
+        Pipeline &P = ctx->main;
+        P.shard_sorted = true;
+        P.shard_rows_out = out_rows;
+        try {
+            P.run(points, n, d, K, out_ids, out_dist, nullptr, 0, pos_begin, pos_end);
+        } catch (...) {
+            P.shard_sorted = false;
+            P.shard_rows_out = nullptr;
+            throw;
+        }
+        P.shard_sorted = false;
+        P.shard_rows_out = nullptr;
     });
 }
 

@@ -71,6 +71,7 @@ struct ScanArgs {
     int self;                  // 1: self-join (a query's own point is not its neighbour)
     float rcap;                // > 0: certificate radius capped at this (the paper's policy)
     int64_t row0;              // first output row held by out_ids/out_dist (chunked output)
+    int sorted_rows;           // 1: output rows by sorted query position (cost-balanced shards)
     int64_t out_rows;          // output rows held (bounds of the checked build)
     int64_t nq;                // queries (sorted query positions < nq)
     int64_t nactive;           // entries of `active`
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan(ScanArgs a)
                 }
             }
             if (certified) {
-                const int64_t rowq = (int64_t)a.qperm[qs] - a.row0;
+                const int64_t rowq = (int64_t)(a.sorted_rows ? qs : a.qperm[qs]) - a.row0;
                 const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
                 const bool rowok = KNN_GUARD(rowin, 9) && rowin;
                 const int64_t row = rowq * K;

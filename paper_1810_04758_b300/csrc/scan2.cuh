@@ -1128,7 +1128,7 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
             if (!certified && lane == 0) a.seed[qsv[i]] = band_thr(vk | SLOT);
             if (certified) {
                 flag = 0;
-                const int64_t rowq = (int64_t)a.qperm[qsv[i]] - a.row0;
+                const int64_t rowq = (int64_t)(a.sorted_rows ? qsv[i] : a.qperm[qsv[i]]) - a.row0;
                 const bool rowin = rowq >= 0 && rowq < a.out_rows;  // checked in every build
                 const bool rowok = KNN_GUARD(rowin, 5) && rowin;
                 const int64_t row = rowq * K;
