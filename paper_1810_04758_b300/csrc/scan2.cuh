@@ -425,6 +425,49 @@ __device__ __forceinline__ uint32_t super_tile_mask(const ScanArgs &a, uint32_t 
     return __ballot_sync(FULL, keep);
 }
 
+// The same test for 32 ranges at once: each lane tests its own range [sb,
+// se) (valid lanes) against every query of the item -- one round of key
+// loads for 32 super-tiles instead of 32 dependent rounds.  Same box, same
+// rounding (the squared gaps summed in dimension order, rounded down) and
+// margin as super_tile_mask.
+template <int DIM>
+__device__ __forceinline__ uint32_t tile_mask_lane(const ScanArgs &a, uint32_t sb, uint32_t se, bool valid,
+                                                   const float *qc, int Q)
+{
+    valid = valid && KNN_GUARD(se <= (uint64_t)a.n && sb < se, 3);
+    const uint64_t k0 = valid ? a.keys[sb] : 0, k1 = valid ? a.keys[se - 1] : 0;
+    const uint64_t x = k0 ^ k1;
+    const int hb = x ? 64 - __clzll((long long)x) : 0;  // free low key bits
+    float blo[DIM], bhi[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const int fb = hb > k ? (hb - k + DIM - 1) / DIM : 0;
+        if (fb >= 30) {
+            blo[k] = -__int_as_float(0x7f800000);
+            bhi[k] = __int_as_float(0x7f800000);
+        } else {
+            int cc = 0;
+            for (int b = fb; b < a.bits; ++b) cc |= (int)((k0 >> (b * DIM + k)) & 1u) << b;
+            blo[k] = face_of(cc, a.lo[k], a.w0);
+            bhi[k] = face_of(cc + (1 << fb), a.lo[k], a.w0);
+        }
+    }
+    uint32_t m = 0;
+    for (int i = 0; i < Q; ++i) {
+        float q[DIM], thr;
+        uint32_t qs;
+        load_query_row<DIM>(qc, i, q, thr, qs);
+        float lb = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float g = fmaxf(fmaxf(__fsub_rd(blo[k], q[k]), __fsub_rd(q[k], bhi[k])), 0.0f);
+            lb = __fadd_rd(lb, __fmul_rd(g, g));
+        }
+        if (!(lb > thr * (1.0f + 0x1p-19f))) m |= 1u << i;
+    }
+    return valid ? m : 0u;
+}
+
 // Score one tile (lane = candidate s with coordinates c, `valid` lanes only)
 // against the queries in `tmask` and append the accepted ones to their buffers.
 template <int DIM, int E>
@@ -825,66 +868,48 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
             const uint32_t sq = qsv[0];
             const int u0 = (a.self && sq >= cb && sq < ce) ? (int)((sq - cb) / S2_SUPER) : 0;
             if constexpr (MEGA) {
-                // two cursors walk outwards from u0 (hi up, lo down),
-                // taking turns; entering a mega-tile, a cursor tests its
-                // box first and jumps over it when no query can use it
-                // (thresholds only fall, so a skipped group stays useless)
-                int hi = u0, lo = u0 - 1, mhi = -1, mlo = -1;
-                bool up = true;
-                while (hi < nst || lo >= 0) {
-                    int u;
-                    if (lo < 0 || (up && hi < nst)) {
-                        u = hi;
-                        const int M = u / S2_MEGA;
-                        if (M != mhi) {
-                            mhi = M;
-                            const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
-                            const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
-                            if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
-                                hi = (M + 1) * S2_MEGA;
-                                up = false;
-                                continue;
-                            }
-                        }
-                        ++hi;
-                    } else {
-                        u = lo;
-                        const int M = u / S2_MEGA;
-                        if (M != mlo) {
-                            mlo = M;
-                            const uint32_t mb = cb + (uint32_t)(M * S2_MEGA) * S2_SUPER;
-                            const uint32_t me = min(mb + (uint32_t)S2_MEGA * S2_SUPER, ce);
-                            if (!(super_tile_mask<DIM>(a, mb, me, qc, Q, lane) & cmk)) {
-                                lo = M * S2_MEGA - 1;
-                                up = true;
-                                continue;
-                            }
-                        }
-                        --lo;
+                // super-tiles visited outwards from u0 (u0, u0 + 1, u0 - 1,
+                // u0 + 2, ...) in rounds of 32: each lane tests the box of one
+                // super-tile of the round against every query of the item,
+                // and the tiles some query can use are scanned in walk order
+                // (a tile's mask is from the round's start: thresholds only
+                // fall, so it keeps every query that can still use it)
+                const int above = nst - 1 - u0, below = u0;
+                const int mlo = min(above, below);
+                for (int base = 0; base < nst; base += 32) {
+                    const int w = base + lane;
+                    const bool valid = w < nst;
+                    int u = 0;
+                    if (valid) {
+                        if (w <= 2 * mlo) u = (w & 1) ? u0 + (w + 1) / 2 : u0 - w / 2;
+                        else u = above > below ? u0 + (w - mlo) : u0 - (w - mlo);
                     }
-                    up = !up;
-                    const uint32_t sb = cb + (uint32_t)u * S2_SUPER;
-                    const uint32_t se = min(sb + (uint32_t)S2_SUPER, ce);
-                    const uint32_t smask = super_tile_mask<DIM>(a, sb, se, qc, Q, lane) & cmk;
-                    KNN_CNT(7, 1);
-                    if (!smask) continue;
-                    KNN_CNT(6, 1);
-                    if (DIM >= S2_WIDE_DIM) {
-                        // two tiles per step, as for the flattened runs
-                        for (uint32_t t0 = sb; t0 < se; t0 += 64) {
-                            const bool vA = t0 + lane < se, vB = t0 + 32 + lane < se;
-                            const uint32_t sA = vA ? t0 + lane : 0u, sB = vB ? t0 + 32 + lane : 0u;
-                            float cA[DIM], cB[DIM];
+                    const uint32_t lsb = cb + (uint32_t)u * S2_SUPER;
+                    const uint32_t lse = min(lsb + (uint32_t)S2_SUPER, ce);
+                    const uint32_t lm = tile_mask_lane<DIM>(a, lsb, lse, valid, qc, Q) & cmk;
+                    KNN_CNT(7, __popc(__ballot_sync(FULL, valid)));
+                    for (uint32_t todo = __ballot_sync(FULL, lm != 0); todo; todo &= todo - 1) {
+                        const int src = __ffs(todo) - 1;
+                        const uint32_t smask = __shfl_sync(FULL, lm, src);
+                        const uint32_t sb = __shfl_sync(FULL, lsb, src), se = __shfl_sync(FULL, lse, src);
+                        KNN_CNT(6, 1);
+                        if (DIM >= S2_WIDE_DIM) {
+                            // two tiles per step, as for the flattened runs
+                            for (uint32_t t0 = sb; t0 < se; t0 += 64) {
+                                const bool vA = t0 + lane < se, vB = t0 + 32 + lane < se;
+                                const uint32_t sA = vA ? t0 + lane : 0u, sB = vB ? t0 + 32 + lane : 0u;
+                                float cA[DIM], cB[DIM];
 #pragma unroll
-                            for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
-                            if (vA) load_point<DIM>(a.xsort, sA, cA);
-                            if (vB) load_point<DIM>(a.xsort, sB, cB);
-                            st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
-                            KNN_ITEM_TILE(__popc(smask) * 2);
-                            scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
+                                for (int k = 0; k < DIM; ++k) cA[k] = cB[k] = __int_as_float(0x7fc00000);
+                                if (vA) load_point<DIM>(a.xsort, sA, cA);
+                                if (vB) load_point<DIM>(a.xsort, sB, cB);
+                                st_cand += (unsigned long long)__popc(smask) * ((vA ? 1u : 0u) + (vB ? 1u : 0u));
+                                KNN_ITEM_TILE(__popc(smask) * 2);
+                                scan2_tile_wide<DIM, E>(cA, cB, sA, sB, smask, buf, qc, hist, my_cnt, K, lane KNN_CNT_ARG);
+                            }
+                        } else {
+                            scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
                         }
-                    } else {
-                        scan2_super_tile<DIM, E>(a, sb, se, smask, buf, qc, hist, my_cnt, K, lane, st_cand KNN_CNT_ARG);
                     }
                 }
             } else {
