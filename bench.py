@@ -971,17 +971,22 @@ def run_served(args, rank, world, local_rank):
     kbuild.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    jobs = gen.served_jobs(args.jobs or 120, seed=0)
-    pts = [torch.from_numpy(gen.served_points(j)).to(dev) for j in jobs]
+    jobs = gen.served_jobs(args.jobs or 500, seed=0)
+    hosts = [gen.served_points(j) for j in jobs]
+    pts = [torch.from_numpy(p).to(dev) for p in hosts]
     Ks = [j["K"] for j in jobs]
-    outs = [(torch.empty((len(p), K), dtype=torch.int32, device=dev),
-             torch.empty((len(p), K), dtype=torch.float64, device=dev)) for p, K in zip(pts, Ks)]
     nq = sum(len(p) for p in pts)
     torch.cuda.synchronize()
+    # results of these jobs are kept and checked against the oracle on
+    # sampled rows (the smallest, the largest and a spread between)
+    by_size = sorted(range(len(jobs)), key=lambda k: len(hosts[k]))
+    check_jobs = sorted(set(by_size[:: max(1, len(jobs) // 6)] + [by_size[-1]]))
 
-    def serve(workers, rate, large_first=False):
+    def serve(workers, rate, large_first=False, keep=()):
         """Submit job k at its Poisson arrival time (rate jobs/s; 0 = all at
-        once), poll until done; returns (makespan s, latencies ms)."""
+        once), poll until done; returns (makespan s, latencies ms, kept
+        outputs).  Outputs are allocated at submission and released when
+        the job is done (as a server holds only the jobs in flight)."""
         ctx = kj.Context(device=local_rank, workers=workers, large_first=large_first)
         # warm the worker pipelines
         for k in range(min(len(jobs), workers)):
@@ -989,14 +994,17 @@ def run_served(args, rank, world, local_rank):
         u = np.array([j["u_arrival"] for j in jobs])
         gaps = -np.log1p(-u) / rate if rate > 0 else np.zeros(len(jobs))
         arrivals = np.cumsum(gaps)
-        pending, lat = {}, {}
+        pending, lat, live, kept = {}, {}, {}, {}
         t0 = time.perf_counter()
         k = 0
         while k < len(jobs) or pending:
             now = time.perf_counter() - t0
-            while k < len(jobs) and arrivals[k] <= now:
-                jid, _, _ = ctx.submit(pts[k], Ks[k], *outs[k])
+            # (all at once: at most 64 in flight, which saturates the pool
+            # without holding every job's outputs at the same time)
+            while k < len(jobs) and arrivals[k] <= now and (rate > 0 or len(pending) < 64):
+                jid, oi, od = ctx.submit(pts[k], Ks[k])
                 pending[jid] = k
+                live[jid] = (oi, od)
                 k += 1
             for jid in list(pending):
                 # a finished job has its wall time set; read it, then retire
@@ -1008,20 +1016,37 @@ def run_served(args, rank, world, local_rank):
                 st = ctx.poll(jid)
                 if st != kj.KNN_OK:
                     raise RuntimeError(f"job failed: {ctx.last_error()}")
-                lat[pending.pop(jid)] = stats.ms_wall
+                kk = pending.pop(jid)
+                lat[kk] = stats.ms_wall
+                o = live.pop(jid)
+                if kk in keep:
+                    kept[kk] = o
             time.sleep(0.0002)
         span = time.perf_counter() - t0
         ctx.close()
-        return span, lat
+        return span, lat, kept
 
-    span_cap, _ = serve(args.workers or 8, 0.0)
+    span_cap, _, kept = serve(args.workers or 8, 0.0, keep=check_jobs)
     capacity = len(jobs) / span_cap
+    # sampled rows of served results against the oracle's brute force
+    checked = 0
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        for kk in check_jobs:
+            p = hosts[kk]
+            rows = np.linspace(0, len(p) - 1, 24).astype(np.int64)
+            wi, wd = oracle.bf_rows(p, Ks[kk], rows)
+            gi, gd = kept[kk][0].cpu().numpy(), kept[kk][1].cpu().numpy()
+            if not (np.array_equal(gi[rows], wi) and np.array_equal(gd[rows], wd)):
+                raise RuntimeError(f"served job {kk}: sampled rows differ from the oracle")
+            checked += len(rows)
+    kept = None
     results = {}
     for rho in (0.5, 0.8, 0.95):
         rate = rho * capacity
-        span, lat = serve(args.workers or 8, rate)
-        span1, lat1 = serve(1, rate)
-        spanp, latp = serve(args.workers or 8, rate, large_first=True)
+        span, lat, _ = serve(args.workers or 8, rate)
+        span1, lat1, _ = serve(1, rate)
+        spanp, latp, _ = serve(args.workers or 8, rate, large_first=True)
         lv = sorted(v for v in lat.values() if v is not None)
         lv1 = sorted(v for v in lat1.values() if v is not None)
         lvp = sorted(v for v in latp.values() if v is not None)
@@ -1046,6 +1071,9 @@ def run_served(args, rank, world, local_rank):
                                f"exponential(40), 1/3 clustered 2-D; Poisson arrivals at rho x "
                                f"capacity", "workers": args.workers or 8},
         "capacity_jobs_per_s": capacity,
+        "oracle_rows_checked": checked,
+        "oracle_check": f"{checked} sampled rows of {len(check_jobs)} served joins (smallest to largest) "
+                        f"equal to the oracle's brute force",
         "by_rho": results,
         "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
         "fifo_baseline": {"q_per_s": top["fifo_q_per_s"], "p50_ms": top["fifo_p50_ms"],
