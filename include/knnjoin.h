@@ -339,6 +339,16 @@ knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t n, int d, 
                                          int32_t *out_ids, double *out_dist, void *stream,
                                          char *errbuf, size_t errlen);
 
+/* Diagnostic: the density-ordered work queue of a self-join's first pass
+ * (Sec. 4.5, Fig. 4: the queries ordered by the number of points in their
+ * grid cell, densest first).  Runs the self-join of points (host or device,
+ * [n][d]; results discarded) and writes to out_sizes (int64, host, cap
+ * entries) the cell count of each query in queue order; *out_len receives
+ * the queue's length (n).  Cells of equal counts follow in (level, cell
+ * key) order.  Size rules as knnjoin_self_join. */
+knnjoin_status knnjoin_work_queue(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int64_t *out_sizes,
+                                  int64_t cap, int64_t *out_len);
+
 /* Library version string. */
 const char *knnjoin_version(void);
 

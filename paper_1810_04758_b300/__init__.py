@@ -35,7 +35,7 @@ EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_jo
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc",
            "knnjoin_fp32_mismatch", "knnjoin_index_create", "knnjoin_index_query",
            "knnjoin_index_stats", "knnjoin_index_destroy", "knnjoin_self_join_rows",
-           "knnjoin_shard_bounds", "knnjoin_self_join_range")
+           "knnjoin_shard_bounds", "knnjoin_self_join_range", "knnjoin_work_queue")
 KNN_NOALLOC_MAX_POINTS = 65536
 
 
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_shard_bounds.restype = I
     lib.knnjoin_self_join_range.argtypes = [P, P, I64, I, I, I64, I64, P, P, P]
     lib.knnjoin_self_join_range.restype = I
+    lib.knnjoin_work_queue.argtypes = [P, P, I64, I, I, P, I64, ctypes.POINTER(ctypes.c_int64)]
+    lib.knnjoin_work_queue.restype = I
     lib.knnjoin_index_create.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.knnjoin_index_create.restype = I
     lib.knnjoin_index_query.argtypes = [P, P, I64, I, P, P]
@@ -224,6 +226,15 @@ def knnjoin_self_join_range(ctx: int, points: int, n: int, d: int, K: int, pos_b
                             out_rows: int, out_ids: int, out_dist: int) -> int:
     return _check(ctx, load_library().knnjoin_self_join_range(ctx, points, n, d, K, pos_begin, pos_end, out_rows,
                                                               out_ids, out_dist))
+
+
+def knnjoin_work_queue(ctx: int, points: int, n: int, d: int, K: int):
+    """Cell count of each query in the first pass's work-queue order."""
+    import numpy as np
+    out = np.zeros(n, np.int64)
+    ln = ctypes.c_int64(0)
+    _check(ctx, load_library().knnjoin_work_queue(ctx, points, n, d, K, out.ctypes.data, n, ctypes.byref(ln)))
+    return out[: ln.value]
 
 
 def gather_shards(n: int, K: int, parts):

@@ -295,6 +295,9 @@ struct Pipeline {
     // each output row to shard_rows_out (int64, host or device)
     bool shard_sorted = false;
     int64_t *shard_rows_out = nullptr;
+    // diagnostic (knnjoin_work_queue): the first pass's work queue, as the
+    // cell count of each query in queue order
+    std::vector<int64_t> *queue_out = nullptr;
     // batched joins scanned together: the scan of each pass goes through this
     // coordinator (one launch over the work items of every join of the batch)
     struct UnionScan *uscan = nullptr;
@@ -1000,6 +1003,16 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             uint32_t ng = pinned[0], maxsz = pinned[1];
             k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
             radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+            if (queue_out && queue_out->empty()) {
+                std::vector<uint32_t> hg(ng + 1), hs(ng);
+                CK(cudaMemcpyAsync(hg.data(), gbegin, sizeof(uint32_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(hs.data(), sval, sizeof(uint32_t) * ng, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                for (uint32_t g = 0; g < ng; ++g) {
+                    const uint32_t sz = hg[hs[g] + 1] - hg[hs[g]];
+                    queue_out->insert(queue_out->end(), sz, (int64_t)sz);
+                }
+            }
             uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
             k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
             scan(nit, ioff, ng);
@@ -1907,6 +1920,31 @@ knnjoin_status knnjoin_self_join_range(knnjoin_ctx *ctx, const float *points, in
         }
         P.shard_sorted = false;
         P.shard_rows_out = nullptr;
+    });
+}
+
+knnjoin_status knnjoin_work_queue(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int64_t *out_sizes,
+                                  int64_t cap, int64_t *out_len)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!points || !out_sizes || !out_len) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        Pipeline &P = ctx->main;
+        CK(cudaSetDevice(P.device));
+        int32_t *ids = P.sc.get<int32_t>("queue_ids", (size_t)n * K);
+        double *dist = P.sc.get<double>("queue_dist", (size_t)n * K);
+        std::vector<int64_t> q;
+        P.queue_out = &q;
+        try {
+            P.run(points, n, d, K, ids, dist);
+        } catch (...) {
+            P.queue_out = nullptr;
+            throw;
+        }
+        P.queue_out = nullptr;
+        *out_len = (int64_t)q.size();
+        memcpy(out_sizes, q.data(), sizeof(int64_t) * (size_t)std::min<int64_t>(cap, (int64_t)q.size()));
     });
 }
 
