@@ -100,23 +100,26 @@ def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
 
 
 def csrc_digest() -> str:
-    """sha256 prefix over the library's CUDA sources (names and bytes)."""
-    import glob
+    """sha256 prefix over the scan kernel's sources: its translation unit
+    (csrc/scan2_launch.cu) and every header it includes (names and bytes)."""
     import hashlib
+    sys.path.insert(0, os.path.join(ROOT, "paper_1810_04758_b300"))
+    from paper_1810_04758_b300 import build as kbuild
+    files = sorted(kbuild._includes(os.path.join(kbuild.CSRC, "scan2_launch.cu"), set()))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1810_04758_b300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(names):
+def profiled_traffic(names, buffers=None):
     """DRAM bytes (read + write) per step of the scan launches of the named
     joins, from the committed ncu counters (profiles/k_scan2_traffic.json);
-    None when a join has none or the CUDA sources changed since they were
-    taken."""
+    None when a join has none, the scan kernel's sources changed since they
+    were taken, or a join now runs with another candidate buffer size
+    (buffers: join -> entries, as the joins ran)."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_scan2_traffic.json")) as f:
             j = json.load(f)
@@ -125,6 +128,8 @@ def profiled_traffic(names):
     if j.get("csrc_sha256_prefix") != csrc_digest():
         return None
     try:
+        if buffers and any(j["joins"][nm].get("buffer_entries") != buffers.get(nm) for nm in names):
+            return None
         return int(sum(j["joins"][nm]["scan_dram_bytes"] for nm in names))
     except (KeyError, TypeError):
         return None
@@ -451,13 +456,15 @@ def run_ours(args, rank, world, local_rank):
             "bound": "alu" if t_fp32 >= t_bytes else "hbm",
             "join_roofline_frac": t_roof / ms_join, "scan_roofline_frac": t_roof / ms_scan_j,
             "fixed_point": st[-1]["fixed_point"], "cell_width": st[-1]["cell_width"],
-            "width_mult": st[-1]["width_mult"], "autotuned": nm in tuned,
+            "width_mult": st[-1]["width_mult"], "buffer_entries": st[-1].get("buffer_entries"),
+            "autotuned": nm in tuned,
         }
     scan_ms_per_step = scan_ms / args.steps
     achieved = alg_flops / (scan_ms_per_step / 1e3) / 1e12 if scan_ms_per_step > 0 else float("nan")
     roofline = {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s",
                 "frac": achieved / p32,
-                "traffic": None if args.configs else profiled_traffic(names),
+                "traffic": None if args.configs else profiled_traffic(
+                    names, {nm: per_summary[nm]["buffer_entries"] for nm in names}),
                 "kernel": "k_scan2",
                 "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
                              f"{sm_max_mhz:.0f} MHz (max SM clock)",
@@ -640,10 +647,22 @@ def run_batched(args, rank, world, local_rank):
     outs_c = [(torch.empty_like(a), torch.empty_like(b)) for a, b in outs_a]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = kj.Context(device=local_rank, stream=stream, workers=args.workers)
+    import tempfile
+    tune_path = args.tune_cache or os.path.join(tempfile.mkdtemp(), "tune_batched.json")
+    ctx = kj.Context(device=local_rank, stream=stream, workers=args.workers, tune_cache_path=tune_path)
+    # autotuning (untimed): one join of each (d, K, floor(log2 n)) class of
+    # the batch, its cell width and buffer size shared by every join of the
+    # class (and by the worker pool)
+    tuned_classes = {}
+    if not args.no_autotune:
+        for p, K in zip(pts, Ks):
+            key = (p.shape[1], K, int(len(p)).bit_length() - 1)
+            if key not in tuned_classes:
+                tuned_classes[key] = ctx.autotune(p, K)
+        torch.cuda.synchronize()
     # the same batch with the joins' scans done together (one launch per
     # (d, buffer size) group and pass over the union of their work items)
-    uctx = kj.Context(device=local_rank, stream=stream, batch_union=True)
+    uctx = kj.Context(device=local_rank, stream=stream, batch_union=True, tune_cache_path=tune_path)
 
     def plain():
         for p, K, (i, d) in zip(pts, Ks, outs_a):
@@ -693,7 +712,8 @@ def run_batched(args, rank, world, local_rank):
         "config": {"workload": f"Batched: {len(jobs)} joins, {nq} points in all, n log-uniform "
                                f"[1k,200k], d in {{2,3,4,6}}, K in {{4,8,16,32,64}}, uniform or "
                                f"exponential(40), seed 0", "workers": args.workers or 8,
-                   "l2": "flushed (256 MiB write) before every timed step"},
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "autotuned_classes": len(tuned_classes)},
         "plain_per_job": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain,
                           "how": "knnjoin_self_join per job, sequentially on one stream"},
         "speedup_vs_plain": ms_plain / ms_batch,

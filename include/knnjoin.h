@@ -144,6 +144,8 @@ typedef struct {
     int64_t pass_candidates[16];   /* candidate distance evaluations of each pass */
     double width_mult;             /* cell-width multiplier the join used */
     int64_t chunks;                /* output chunks (1 unless out_chunk_mb applied) */
+    int64_t buffer_entries;        /* candidate buffer per query in the scan (64, 128 or 256;
+                                      the smallest holding K + 32 unless autotuned larger) */
 } knnjoin_stats;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, own stream).
@@ -247,13 +249,17 @@ knnjoin_status knnjoin_index_query(knnjoin_index *index, const float *queries, i
 knnjoin_status knnjoin_index_stats(knnjoin_index *index, knnjoin_stats *out);
 void knnjoin_index_destroy(knnjoin_index *index);
 
-/* Autotuning (not in the paper; its analogue is the search-distance factor
- * study of Sec. 5.4): time the self-join of these points at a fixed list of
- * cell-width multipliers (1.0 .. 1.625, best of two runs each, outputs in
- * library scratch), keep the fastest for the key (d, K, floor(log2 n)) -- used
- * by later joins of the context (and its worker pool) unless the config fixed
- * width_mult -- and rewrite tune_cache_path if set.  Same validation as
- * knnjoin_self_join; *best_width_mult receives the chosen multiplier. */
+/* Autotuning (not in the paper; its analogues are the search-distance factor
+ * study of Sec. 5.4 and the task-granularity study of Sec. 4.7): time the
+ * self-join of these points at a fixed list of cell-width multipliers (1.0 ..
+ * 1.625, best of two runs each, outputs in library scratch), then at the best
+ * one the next larger candidate buffer per query (e.g. 128 instead of 64
+ * entries for K <= 32, which also halves the queries per work item); keep the
+ * fastest pair for the key (d, K, floor(log2 n)) -- used by later joins of the
+ * context (and its worker pool) unless the config fixed width_mult -- and
+ * rewrite tune_cache_path if set.  Same validation as knnjoin_self_join;
+ * *best_width_mult receives the chosen multiplier (the buffer size is reported
+ * in knnjoin_stats.buffer_entries of later joins). */
 knnjoin_status knnjoin_autotune(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K,
                                 float *best_width_mult);
 

@@ -68,7 +68,8 @@ class KnnjoinStats(ctypes.Structure):
                 ("ms_pass", ctypes.c_double * 16),
                 ("pass_candidates", ctypes.c_int64 * 16),
                 ("width_mult", ctypes.c_double),
-                ("chunks", ctypes.c_int64)]
+                ("chunks", ctypes.c_int64),
+                ("buffer_entries", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}

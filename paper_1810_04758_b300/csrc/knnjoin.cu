@@ -187,6 +187,7 @@ struct NvtxRange {
 struct TuneTable {
     std::mutex mu;
     std::map<std::tuple<int, int, int>, float> wm;
+    std::map<std::tuple<int, int, int>, int> buf;  // tuned candidate-buffer entries / 32 (E), if any
     std::string path;
     float fixed = 0.0f;     // the caller's width_mult (> 0 overrides tuning)
     float dflt = 1.25f;
@@ -204,30 +205,40 @@ struct TuneTable {
         auto it = wm.find(std::make_tuple(d, K, nlog2(n)));
         return it == wm.end() ? dflt : it->second;
     }
-    void set(int d, int K, int64_t n, float v)
+    // tuned buffer size E for (d, K, n), 0 = the default (the smallest holding K + 32)
+    int lookup_E(int d, int K, int64_t n)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = buf.find(std::make_tuple(d, K, nlog2(n)));
+        return it == buf.end() ? 0 : it->second;
+    }
+    void set(int d, int K, int64_t n, float v, int E = 0)
     {
         std::lock_guard<std::mutex> lk(mu);
         wm[std::make_tuple(d, K, nlog2(n))] = v;
+        if (E > 0) buf[std::make_tuple(d, K, nlog2(n))] = E;
         save_locked();
     }
-    // {"knnjoin_tune": 1, "entries": [{"d": 2, "K": 32, "nlog2": 20, "width_mult": 1.125}, ...]}
+    // {"knnjoin_tune": 1, "entries": [{"d": 2, "K": 32, "nlog2": 20, "width_mult": 1.125, "buffer": 2}, ...]}
     void load()
     {
         if (path.empty()) return;
         FILE *f = fopen(path.c_str(), "r");
         if (!f) return;
         std::string text;
-        char buf[4096];
-        size_t got;
-        while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+        char chunk[4096];
+        size_t nread;
+        while ((nread = fread(chunk, 1, sizeof(chunk), f)) > 0) text.append(chunk, nread);
         fclose(f);
         std::lock_guard<std::mutex> lk(mu);
         for (size_t at = text.find("{\"d\":"); at != std::string::npos; at = text.find("{\"d\":", at + 1)) {
             int d = 0, K = 0, nl = 0;
             float v = 0.0f;
-            if (sscanf(text.c_str() + at, "{\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %f", &d, &K,
-                       &nl, &v) == 4 && v > 0.0f && v < 16.0f)
-                wm[std::make_tuple(d, K, nl)] = v;
+            int E = 0;
+            const int got = sscanf(text.c_str() + at, "{\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %f, "
+                                   "\"buffer\": %d", &d, &K, &nl, &v, &E);
+            if (got >= 4 && v > 0.0f && v < 16.0f) wm[std::make_tuple(d, K, nl)] = v;
+            if (got == 5 && (E == 2 || E == 4 || E == 8)) buf[std::make_tuple(d, K, nl)] = E;
         }
     }
     void save_locked()
@@ -238,8 +249,10 @@ struct TuneTable {
         fprintf(f, "{\"knnjoin_tune\": 1, \"entries\": [");
         bool first = true;
         for (auto &e : wm) {
-            fprintf(f, "%s\n {\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %.6g}", first ? "" : ",",
-                    std::get<0>(e.first), std::get<1>(e.first), std::get<2>(e.first), e.second);
+            auto b = buf.find(e.first);
+            fprintf(f, "%s\n {\"d\": %d, \"K\": %d, \"nlog2\": %d, \"width_mult\": %.6g, \"buffer\": %d}",
+                    first ? "" : ",", std::get<0>(e.first), std::get<1>(e.first), std::get<2>(e.first), e.second,
+                    b == buf.end() ? 0 : b->second);
             first = false;
         }
         fprintf(f, "\n]}\n");
@@ -272,6 +285,7 @@ struct Pipeline {
     float width_mult = 1.25f;      // used when no tune table is attached
     TuneTable *tune = nullptr;
     float force_wm = 0.0f;         // > 0: this multiplier (autotuning runs)
+    int force_E = 0;               // > 0: this buffer size (autotuning runs)
     int policy = 0;                // knnjoin_config.policy
     int tail_queries = 0;          // knnjoin_config.tail_queries
     size_t out_chunk_bytes = 0;    // knnjoin_config.out_chunk_mb (0: automatic)
@@ -949,7 +963,15 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         const size_t smem1 = scan_smem_bytes(d, noff, CH, B1);
         // fast kernel (scan2.cuh)
         const bool fast = K + 32 <= 256;
-        const int E2 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
+        // candidate buffer of 32 * E2 entries per query: the smallest holding
+        // K + 32, or a larger one the autotuner found faster for this class
+        const int E2min = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
+        int E2 = E2min;
+        {
+            const int tE = force_E > 0 ? force_E : (tune && policy == 0 ? tune->lookup_E(d, K, n) : 0);
+            if (tE >= E2min && tE <= 8) E2 = tE;
+        }
+        stats.buffer_entries = 32 * E2;
         const int QM = scan2_queries_per_item(E2);
         const size_t smem2 = scan2_smem_bytes(d, QM, E2);
 
@@ -2054,22 +2076,38 @@ knnjoin_status knnjoin_autotune(knnjoin_ctx *ctx, const float *points, int64_t n
         int32_t *ids = P.sc.get<int32_t>("tune_ids", (size_t)n * K);
         double *dist = P.sc.get<double>("tune_dist", (size_t)n * K);
         static const float cand[] = {1.0f, 1.0625f, 1.125f, 1.1875f, 1.25f, 1.3125f, 1.4f, 1.5f, 1.625f};
-        float best = ctx->tune.dflt;
-        double best_ms = 1e300;
-        for (float c : cand) {
-            P.force_wm = c;
+        auto time_join = [&] {
             double ms = 1e300;
             for (int rep = 0; rep < 2; ++rep) {
                 P.run(points, n, d, K, ids, dist);
                 ms = std::min(ms, (double)P.stats.ms_total);
             }
+            return ms;
+        };
+        // the cell-width multiplier at the default buffer size ...
+        const int E0 = K + 32 <= 64 ? 2 : (K + 32 <= 128 ? 4 : 8);
+        P.force_E = E0;
+        float best = ctx->tune.dflt;
+        double best_ms = 1e300;
+        for (float c : cand) {
+            P.force_wm = c;
+            const double ms = time_join();
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
             }
         }
+        // ... then, at that multiplier, the next larger buffer (half as many
+        // queries per work item, more room before a shrink)
+        int bestE = E0;
+        if (2 * E0 <= 8) {
+            P.force_wm = best;
+            P.force_E = 2 * E0;
+            if (time_join() < best_ms) bestE = 2 * E0;
+        }
         P.force_wm = 0.0f;
-        if (ctx->tune.fixed <= 0.0f) ctx->tune.set(d, K, n, best);
+        P.force_E = 0;
+        if (ctx->tune.fixed <= 0.0f) ctx->tune.set(d, K, n, best, bestE);
         *best_width_mult = best;
     });
 }

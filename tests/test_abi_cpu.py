@@ -61,7 +61,8 @@ def test_struct_layouts_match_header(tmp_path):
     assert lines["stats"] == [ctypes.sizeof(kj.KnnjoinStats), kj.KnnjoinStats.candidates.offset,
                               kj.KnnjoinStats.ms_index.offset, kj.KnnjoinStats.ms_wall.offset,
                               kj.KnnjoinStats.ms_pass.offset, kj.KnnjoinStats.pass_candidates.offset,
-                              kj.KnnjoinStats.width_mult.offset, kj.KnnjoinStats.chunks.offset]
+                              kj.KnnjoinStats.width_mult.offset, kj.KnnjoinStats.chunks.offset,
+                              kj.KnnjoinStats.buffer_entries.offset]
 
 
 def test_exact_arithmetic_matches_ieee_double_on_host(tmp_path):
