@@ -64,7 +64,11 @@ typedef enum {
 typedef struct {
     int device;               /* CUDA device ordinal */
     void *stream;             /* cudaStream_t to run on; NULL = the context makes its own */
-    void *(*alloc)(size_t bytes, void *user);  /* optional device allocator */
+    void *(*alloc)(size_t bytes, void *user);  /* optional device allocator: returns device memory
+                                                   of the context's GPU, 256-byte aligned as
+                                                   cudaMalloc's, or NULL (KNN_ERR_NOMEM); a pointer
+                                                   not 16-byte aligned is freed and the call fails
+                                                   with KNN_ERR_INVALID */
     void (*free)(void *ptr, void *user);       /* matching free */
     void *user;
     size_t hbm_budget_bytes;  /* admission limit of batched/served jobs; 0 = 90% of free memory */

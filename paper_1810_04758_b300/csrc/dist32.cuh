@@ -67,6 +67,14 @@ __device__ __forceinline__ unsigned long long f32x2_add(unsigned long long a, un
     return r;
 }
 
+// Packed sum rounded towards -inf (each half as __fadd_rd).
+__device__ __forceinline__ unsigned long long f32x2_add_rd(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 // dist2_f32(q, cA) and dist2_f32(q, cB), with cp[k] = (cA[k], cB[k]) packed.
 template <int DIM>
 __device__ __forceinline__ void dist2_f32_x2(const float (&q)[DIM], const unsigned long long (&cp)[DIM], float &dA,
@@ -91,6 +99,33 @@ __device__ __forceinline__ void dist2_f32_x2(const float (&q)[DIM], const unsign
         else e = f32x2_fma(df, df, e);
     }
     f32x2_unpack(f32x2_add(e, o), dA, dB);
+}
+
+// dist2_f32(q0, c) and dist2_f32(q1, c) for two queries and one candidate:
+// qp[k] = (q0[k], q1[k]) and cc[k] = (c[k], c[k]) packed.
+template <int DIM>
+__device__ __forceinline__ void dist2_f32_x2q(const unsigned long long (&qp)[DIM], const unsigned long long (&cc)[DIM],
+                                              float &d0, float &d1)
+{
+    const unsigned long long z = 0ull;  // (+0, +0)
+    if (DIM < 4) {
+        unsigned long long d2 = z;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const unsigned long long df = f32x2_sub(qp[k], cc[k]);
+            d2 = f32x2_fma(df, df, d2);
+        }
+        f32x2_unpack(d2, d0, d1);
+        return;
+    }
+    unsigned long long e = z, o = z;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const unsigned long long df = f32x2_sub(qp[k], cc[k]);
+        if (k & 1) o = f32x2_fma(df, df, o);
+        else e = f32x2_fma(df, df, e);
+    }
+    f32x2_unpack(f32x2_add(e, o), d0, d1);
 }
 
 }  // namespace knn

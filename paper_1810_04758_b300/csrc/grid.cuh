@@ -128,40 +128,75 @@ __global__ void k_eps_rows(const float *__restrict__ xs, int64_t n, int d, int64
     }
 }
 
-__device__ __forceinline__ float row_dist(const float *a, const float *b, int d)
+// Squared distance of two sampled rows over their first P floats (P = 4
+// for d <= 4, else 8).  The rows are zero beyond d, and fmaf(0, 0, s) = s,
+// so this is the d-term sum exactly.
+template <int P>
+__device__ __forceinline__ float row_d2(const float4 *a, const float (&b)[P])
 {
     float s = 0.0f;
-    for (int k = 0; k < d; ++k) {
-        const float t = a[k] - b[k];
-        s = fmaf(t, t, s);
+#pragma unroll
+    for (int v = 0; v < P / 4; ++v) {
+        const float4 t = a[v];
+        const float x[4] = {t.x - b[4 * v], t.y - b[4 * v + 1], t.z - b[4 * v + 2], t.w - b[4 * v + 3]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s = fmaf(x[k], x[k], s);
     }
-    return sqrtf(s);
+    return s;
+}
+
+// A bound every s with sqrtf(s) < r lies below: sqrtf rounds correctly and r
+// is a float, so sqrtf(s) < r means sqrt(s) < r, i.e. s < r^2 <= this bound
+// (r^2 (1 + 2^-20), rounded up).  Larger s skip the square root.
+__device__ __forceinline__ float below_bound(float r) { return __fmul_ru(__fmul_ru(r, r), 1.0f + 0x1p-20f); }
+
+// The sample index of subset point j's own point (-1 if it is not a sample).
+__device__ __forceinline__ int64_t self_sample(int64_t j, int64_t mstride, int64_t sstride)
+{
+    const int64_t p = j * mstride;
+    return p % sstride == 0 ? p / sstride : -1;
+}
+
+// Samples [i0, i1) of slice blockIdx.y (gridDim.y slices of the S samples).
+__device__ __forceinline__ void sample_slice(int64_t S, int64_t &i0, int64_t &i1)
+{
+    const int64_t per = (S + gridDim.y - 1) / gridDim.y;
+    i0 = (int64_t)blockIdx.y * per;
+    i1 = min(S, i0 + per);
 }
 
 // Histogram of distances from the S sample points to the m subset points,
 // bins of width range / 1024 over [0, range), where range = eps_mean (stage
 // 0) or twice the stage-0 estimate (stage 1).  A thread holds one subset
-// point and walks the samples (staged in shared memory).
-__global__ void k_eps_hist(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n, int d,
+// point and walks its block's slice of the samples (staged in shared
+// memory); the block's histogram is added to the global one.
+template <int P>
+__global__ void k_eps_hist(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n,
                            int64_t S, int64_t m, const GridParams *gp, PrepReduce *red, int stage)
 {
     __shared__ unsigned h[1024];
-    __shared__ float sp[256 * 8];
+    __shared__ float4 sp[256 * 2];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
-    for (int i = threadIdx.x; i < (int)S * 8; i += blockDim.x) sp[i] = srow[i];
+    for (int i = threadIdx.x; i < (int)S * 2; i += blockDim.x) sp[i] = ((const float4 *)srow)[i];
     __syncthreads();
     const float range = stage == 0 ? gp->eps_mean : 2.0f * gp->eps_min;
     if (range > 0.0f) {
-        const float inv_bw = 1024.0f / range;
+        const float inv_bw = 1024.0f / range, r2 = below_bound(range);
         const int64_t sstride = n / S, mstride = n / m;
+        int64_t i0, i1;
+        sample_slice(S, i0, i1);
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
              j += (int64_t)gridDim.x * blockDim.x) {
-            float p[8];
-            for (int k = 0; k < 8; ++k) p[k] = mrow[j * 8 + k];
-            for (int64_t i = 0; i < S; ++i) {
-                if (i * sstride == j * mstride) continue;
-                const float dd = row_dist(sp + i * 8, p, d);
-                if (dd < range) atomicAdd(&h[min((int)(dd * inv_bw), 1023)], 1u);
+            float p[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) p[k] = mrow[j * 8 + k];
+            const int64_t own = self_sample(j, mstride, sstride);
+            for (int64_t i = i0; i < i1; ++i) {
+                const float s2 = row_d2<P>(sp + i * 2, p);
+                if (s2 < r2 && i != own) {
+                    const float dd = sqrtf(s2);
+                    if (dd < range) atomicAdd(&h[min((int)(dd * inv_bw), 1023)], 1u);
+                }
             }
         }
     }
@@ -181,29 +216,36 @@ struct ParamsIn {
 
 // Density skew: neighbours of each sampled point among the subset within
 // the radius where about K are expected (eps_min scaled by (n/m)^(1/d)).
-// A thread holds one subset point; per sample, a warp ballot counts its
-// lanes within the radius.
+// A thread holds one subset point and walks its block's slice of the
+// samples; per sample, a warp ballot counts its lanes within the radius.
+template <int P>
 __global__ void k_eps_count(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n, int d,
                             int64_t S, int64_t m, const GridParams *gp, PrepReduce *red)
 {
     __shared__ unsigned cnt[256];
-    __shared__ float sp[256 * 8];
+    __shared__ float4 sp[256 * 2];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
-    for (int i = threadIdx.x; i < (int)S * 8; i += blockDim.x) sp[i] = srow[i];
+    for (int i = threadIdx.x; i < (int)S * 2; i += blockDim.x) sp[i] = ((const float4 *)srow)[i];
     __syncthreads();
     const float e = gp->eps_min * powf((float)n / (float)m, 1.0f / (float)d);
     if (e > 0.0f && isfinite(e)) {
+        const float e2 = below_bound(e);
         const int64_t sstride = n / S, mstride = n / m;
+        int64_t i0, i1;
+        sample_slice(S, i0, i1);
         // every lane of a warp runs the same number of rounds (ballots)
         const int64_t span = (int64_t)gridDim.x * blockDim.x;
         const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
         for (int64_t base = first; base < m; base += span) {
             const int64_t j = base + (threadIdx.x & 31);
             const bool valid = j < m;
-            float p[8];
-            for (int k = 0; k < 8; ++k) p[k] = valid ? mrow[j * 8 + k] : 0.0f;
-            for (int64_t i = 0; i < S; ++i) {
-                const bool in = valid && i * sstride != j * mstride && row_dist(sp + i * 8, p, d) < e;
+            float p[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) p[k] = valid ? mrow[j * 8 + k] : 0.0f;
+            const int64_t own = valid ? self_sample(j, mstride, sstride) : -1;
+            for (int64_t i = i0; i < i1; ++i) {
+                const float s2 = row_d2<P>(sp + i * 2, p);
+                const bool in = valid && i != own && s2 < e2 && sqrtf(s2) < e;
                 const unsigned b = __ballot_sync(FULL, in);
                 if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt[i], (unsigned)__popc(b));
             }
@@ -214,16 +256,21 @@ __global__ void k_eps_count(const float *__restrict__ srow, const float *__restr
         if (cnt[i]) atomicAdd(&red->scount[i], cnt[i]);
 }
 
-__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in);
+__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in, double csum,
+                              unsigned cmaxs);
 
 // stage 0: eps_mean and the grid-independent fields; stage 1: eps_min
 // estimate from hist[0]; stage 2: refined eps_min from hist[1]; stage 3:
-// density skew, cell side, grid and key bits.
+// density skew, cell side, grid and key bits.  One warp: the bin search and
+// the sample sums are spread over the lanes (integer sums, exact in any
+// order), the rest runs on lane 0.
 __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int stage)
 {
-    if (threadIdx.x || blockIdx.x) return;
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x || threadIdx.x >= 32) return;
     const int d = in.d;
     if (stage == 0) {
+        if (lane) return;
         gp->n = (int)in.n;
         gp->d = d;
         gp->K = in.K;
@@ -245,22 +292,51 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
         return;
     }
     if (stage == 3) {
-        k_params_grid(red, gp, in);
+        // sampled points' neighbour counts: their sum and maximum
+        unsigned long long cs = 0;
+        unsigned cm = 0;
+        for (int i = lane; i < (int)in.S && i < 256; i += 32) {
+            cs += red->scount[i];
+            cm = max(cm, red->scount[i]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            cs += __shfl_xor_sync(FULL, cs, o);
+            cm = max(cm, __shfl_xor_sync(FULL, cm, o));
+        }
+        if (lane == 0) k_params_grid(red, gp, in, (double)cs, cm);
         return;
     }
-    // cumulative count per sampled point reaches K (scaled to the subset)
+    // the first bin at which the cumulative count per sampled point reaches
+    // K (scaled to the subset): lane l sums bins [32 l, 32 l + 32), a warp
+    // prefix sum finds the lane whose chunk crosses the target, that lane
+    // finds the bin
     const unsigned *h = red->hist[stage - 1];
-    float range = stage == 1 ? gp->eps_mean : 2.0f * gp->eps_min;
-    double target = (double)in.K * (double)in.S * (double)in.m / (double)(in.n - 1);
-    double cum = 0.0;
-    int pick = -1;
-    for (int b = 0; b < 1024; ++b) {
-        cum += h[b];
-        if (cum >= target) {
-            pick = b;
-            break;
-        }
+    const float range = stage == 1 ? gp->eps_mean : 2.0f * gp->eps_min;
+    const double target = (double)in.K * (double)in.S * (double)in.m / (double)(in.n - 1);
+    unsigned long long own = 0;
+    for (int b = 0; b < 32; ++b) own += h[lane * 32 + b];
+    unsigned long long inc = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
     }
+    const unsigned cross = __ballot_sync(FULL, (double)inc >= target);
+    int pick = -1;
+    if (cross) {
+        const int src = __ffs(cross) - 1;
+        if (lane == src) {
+            unsigned long long cum = inc - own;
+            for (int b = 0; b < 32; ++b) {
+                cum += h[lane * 32 + b];
+                if ((double)cum >= target) {
+                    pick = lane * 32 + b;
+                    break;
+                }
+            }
+        }
+        pick = __shfl_sync(FULL, pick, src);
+    }
+    if (lane) return;
     float eps = pick >= 0 ? (pick + 0.5f) * (range / 1024.0f) : range;
     if (stage == 1) {
         gp->eps_min = eps;
@@ -270,7 +346,8 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
     gp->eps_min = eps;
 }
 
-__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in)
+__device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const ParamsIn &in, double csum,
+                              unsigned cmaxs)
 {
     const int d = in.d;
     const float eps = gp->eps_min;
@@ -283,12 +360,6 @@ __device__ void k_params_grid(const PrepReduce *red, GridParams *gp, const Param
     int bmax = min(24, 63 / d);
     // levels finer than the search-distance width, from the density skew of
     // the sampled points: the densest sample over the mean, per dimension
-    double csum = 0.0;
-    unsigned cmaxs = 0;
-    for (int s = 0; s < (int)in.S && s < 256; ++s) {
-        csum += red->scount[s];
-        cmaxs = max(cmaxs, red->scount[s]);
-    }
     int finer = 0;
     if (csum > 0.0) {
         double ratio = (double)cmaxs * (double)min((int64_t)256, in.S) / csum;

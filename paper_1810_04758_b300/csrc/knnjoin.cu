@@ -90,6 +90,10 @@ struct Allocator {
             if (!p)
                 fail(KNN_ERR_NOMEM, nomem_msg ? std::string(nomem_msg)
                                               : "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+            if ((uintptr_t)p & 15) {  // kernels read scratch with 16-byte vector loads
+                if (free) free(p, user);
+                fail(KNN_ERR_INVALID, "allocator hook returned a pointer not aligned to 16 bytes");
+            }
             return p;
         }
         cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
@@ -835,13 +839,22 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         float *srow = sc.get<float>("eps_srow", (size_t)pin.S * 8);
         float *mrow = sc.get<float>("eps_mrow", (size_t)pin.m * 8);
         k_eps_rows<<<grid_for(pin.S + pin.m, 256, nsm), 256, 0, s>>>(xs, n, d, pin.S, pin.m, srow, mrow); ++launches;
-        const unsigned gm = (unsigned)((pin.m + 255) / 256);
+        // subset points x slices of the samples (4 slices: enough warps to
+        // fill the GPU at m = 65,536)
+        const dim3 gm((unsigned)((pin.m + 255) / 256), 4);
+        const bool p4 = d <= 4;  // rows compared over 4 floats, else 8
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
-        k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 0); ++launches;
+        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0);
+        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0);
+        ++launches;
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
-        k_eps_hist<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, 1); ++launches;
+        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1);
+        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1);
+        ++launches;
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
-        k_eps_count<<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red); ++launches;
+        if (p4) k_eps_count<4><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red);
+        else k_eps_count<8><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red);
+        ++launches;
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
         CK(cudaGetLastError());
         hp = read1(gp);

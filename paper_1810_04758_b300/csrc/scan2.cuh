@@ -340,6 +340,33 @@ static __device__ __noinline__ int2 shrink_buffer(uint64_t *bi, int c0, int K, u
     return make_int2(c1, __float_as_int(nt));
 }
 
+// The query-pair rows and the contiguous thresholds follow the query rows
+// in a warp's shared memory (Scan2Warp).
+template <int DIM, int E>
+__device__ __forceinline__ float *scan2_qq(float *qc)
+{
+    return qc + scan2_queries_per_item(E) * query_row_floats(DIM);
+}
+template <int DIM, int E>
+__device__ __forceinline__ float *scan2_thrv(float *qc)
+{
+    return scan2_qq<DIM, E>(qc) + qpair_floats(DIM, scan2_queries_per_item(E), E);
+}
+// The bound a neighbour cell's rounded-down squared distance must not
+// exceed for a query of threshold t: t with a 2^-19 margin for the FP32
+// rounding of candidate distances.
+__device__ __forceinline__ float cell_test_thr(float t) { return t * (1.0f + 0x1p-19f); }
+
+// Query i's threshold, in every copy (its row, its query pair's row) and
+// its cell-test bound (contiguous, for vector loads).
+template <int DIM, int E>
+__device__ __forceinline__ void scan2_set_thr(float *qc, int i, float t)
+{
+    qc[i * query_row_floats(DIM) + DIM] = t;
+    scan2_thrv<DIM, E>(qc)[i] = cell_test_thr(t);
+    if (scan2_qpair(DIM, E)) scan2_qq<DIM, E>(qc)[(i >> 1) * qpair_row_floats(DIM) + 2 * DIM + (i & 1)] = t;
+}
+
 // Append this tile's accepted candidates (ballot `bal`) to query i's buffer;
 // on overflow shrink it to the band of its K-th value first, and mark the
 // query for the general kernel (count -1, threshold -1) if even that does
@@ -351,7 +378,6 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
 {
     KNN_CNT(9, 1);
     constexpr int B = 32 * E;
-    constexpr int QP = query_row_floats(DIM);
     uint64_t *bi = buf + i * B;
     int c0 = __shfl_sync(FULL, my_cnt, i);
     int nnew = __popc(bal);
@@ -371,10 +397,7 @@ __device__ __forceinline__ void scan2_insert(uint64_t *buf, float *qc, uint32_t 
             acc = false;
             nnew = 0;
         }
-        if (lane == 0) {
-            qc[i * QP + DIM] = tnew;
-            qc[scan2_queries_per_item(E) * QP + i] = tnew;  // the thresholds' copy after the rows
-        }
+        if (lane == 0) scan2_set_thr<DIM, E>(qc, i, tnew);
         __syncwarp();
     }
     if (acc && KNN_GUARD(c0 >= 0 && c0 + __popc(bal & lanemask_lt()) < B, 4))
@@ -573,22 +596,68 @@ __device__ __forceinline__ void scan2_tile_wide(const float (&cA)[DIM], const fl
                                                 uint32_t sB, uint32_t tmask, uint64_t *buf, float *qc,
                                                 uint32_t *hist, int &my_cnt, int K, int lane KNN_CNT_PARAM)
 {
-    // the two candidates' coordinates packed per dimension (once per step)
-    unsigned long long cp[DIM];
+    if constexpr (scan2_qpair(DIM, E)) {
+        // queries two at a time: the pair's row holds each coordinate of
+        // queries 2p and 2p + 1 in one 64-bit word, and each candidate's
+        // coordinate is duplicated into both halves once per step, so one
+        // packed chain gives the candidate's distances to both queries.
+        // Pairs with either query in the mask are scored; the other query
+        // of such a pair is scored too (its cell test is a pruning bound
+        // only, and accepting what its threshold admits keeps its buffer
+        // a superset of that set); a missing query (odd count) has NaN
+        // coordinates and accepts nothing.
+        constexpr int QQ = qpair_row_floats(DIM);
+        const float *qq = scan2_qq<DIM, E>(qc);
+        unsigned long long ca[DIM], cb[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) cp[k] = f32x2_pack(cA[k], cB[k]);
-    for (uint32_t m = tmask; m; m &= m - 1) {
-        const int i = __ffs(m) - 1;
-        float qv[DIM], ti;
-        uint32_t qi_s;
-        load_query_row<DIM>(qc, i, qv, ti, qi_s);
-        float dA, dB;
-        dist2_f32_x2<DIM>(qv, cp, dA, dB);
-        const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
-        const bool accB = dB <= ti && sB != qi_s;
-        // one vote first for d >= 5, where a step usually accepts nothing
-        if (DIM < 5 || __any_sync(FULL, accA || accB))
-            scan2_insert_pair<DIM, E>(buf, qc, hist, my_cnt, i, accA, accB, dA, dB, sA, sB, ti, K, lane KNN_CNT_ARG);
+        for (int k = 0; k < DIM; ++k) {
+            ca[k] = f32x2_pack(cA[k], cA[k]);
+            cb[k] = f32x2_pack(cB[k], cB[k]);
+        }
+        for (uint32_t pm = (tmask | (tmask >> 1)) & 0x55555555u; pm; pm &= pm - 1) {
+            const int i0 = __ffs(pm) - 1;  // even
+            unsigned long long r[QQ / 2];
+            const ulonglong2 *row = (const ulonglong2 *)(qq + (i0 >> 1) * QQ);
+#pragma unroll
+            for (int v = 0; v < QQ / 4; ++v) {
+                const ulonglong2 t = row[v];
+                r[2 * v] = t.x;
+                r[2 * v + 1] = t.y;
+            }
+            unsigned long long qp[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) qp[k] = r[k];
+            float t0, t1, u0f, u1f, dA0, dA1, dB0, dB1;
+            f32x2_unpack(r[DIM], t0, t1);
+            f32x2_unpack(r[DIM + 1], u0f, u1f);
+            const uint32_t u0 = __float_as_uint(u0f), u1 = __float_as_uint(u1f);
+            dist2_f32_x2q<DIM>(qp, ca, dA0, dA1);
+            dist2_f32_x2q<DIM>(qp, cb, dB0, dB1);
+            const bool aA0 = dA0 <= t0 && sA != u0, aB0 = dB0 <= t0 && sB != u0;  // NaN past the end
+            const bool aA1 = dA1 <= t1 && sA != u1, aB1 = dB1 <= t1 && sB != u1;
+            if (DIM < 5 || __any_sync(FULL, aA0 || aB0 || aA1 || aB1)) {
+                scan2_insert_pair<DIM, E>(buf, qc, hist, my_cnt, i0, aA0, aB0, dA0, dB0, sA, sB, t0, K, lane KNN_CNT_ARG);
+                scan2_insert_pair<DIM, E>(buf, qc, hist, my_cnt, i0 + 1, aA1, aB1, dA1, dB1, sA, sB, t1, K, lane KNN_CNT_ARG);
+            }
+        }
+    } else {
+        // the two candidates' coordinates packed per dimension (once per step)
+        unsigned long long cp[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cp[k] = f32x2_pack(cA[k], cB[k]);
+        for (uint32_t m = tmask; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            float qv[DIM], ti;
+            uint32_t qi_s;
+            load_query_row<DIM>(qc, i, qv, ti, qi_s);
+            float dA, dB;
+            dist2_f32_x2<DIM>(qv, cp, dA, dB);
+            const bool accA = dA <= ti && sA != qi_s;  // NaN past the end
+            const bool accB = dB <= ti && sB != qi_s;
+            // one vote first for d >= 5, where a step usually accepts nothing
+            if (DIM < 5 || __any_sync(FULL, accA || accB))
+                scan2_insert_pair<DIM, E>(buf, qc, hist, my_cnt, i, accA, accB, dA, dB, sA, sB, ti, K, lane KNN_CNT_ARG);
+        }
     }
 }
 
@@ -619,7 +688,8 @@ struct Scan2Warp {
     uint64_t *buf;   // [QM][32E]  (d2_32 bits << 32 | sorted index)
     uint64_t *dil;   // [3d] key parts (or dense index terms) of neighbour coordinates
     float *qc;       // [QM][QP] coords, threshold, sorted position
-    float *thrv;     // [QM] the thresholds again, contiguous (vector loads in the cell test)
+    float *qq;       // [QM/2][QQ] query pairs (scan2_qpair): coords, thresholds, positions
+    float *thrv;     // [QM] cell-test bounds of the thresholds, contiguous (vector loads)
     int *cnt;        // [QM]
     uint32_t *qsv;   // [QM]
     uint32_t *hist;  // [256]
@@ -630,16 +700,18 @@ struct Scan2Warp {
     float *gsq;
     float *rcert;    // [QM] certificate radius of each query
     int *cellv;      // [2d] the item's cell and the level's extent
+    static_assert(QM == scan2_queries_per_item(E), "queries per item follow the buffer size");
     __device__ __forceinline__ explicit Scan2Warp(unsigned char *wb)
     {
         buf = (uint64_t *)wb;
         dil = buf + QM * 32 * E;
         qc = (float *)(dil + dil_entries(DIM));
-        thrv = qc + QM * query_row_floats(DIM);
+        qq = qc + QM * query_row_floats(DIM);
+        thrv = qq + qpair_floats(DIM, QM, E);
         cnt = (int *)(thrv + QM);
         qsv = (uint32_t *)(cnt + QM);
         hist = qsv + QM;
-        gsq = (float *)(hist + 256);
+        gsq = (float *)(hist + hist_entries(E));
         rcert = gsq + 3 * DIM * QM;
         cellv = (int *)(rcert + QM);
     }
@@ -784,13 +856,28 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
         const float thr0 = (KNN_PREFILTER_R2 <= 0.0f || isinf(R))
                                ? __int_as_float(0x7f800000)
                                : __fmul_ru(__fmul_ru(R, R), KNN_PREFILTER_R2 * (1.0f + 0x1p-14f));
-        qc[lane * QP + DIM] = thrv[lane] = fminf(thr0, a.seed[qsv[lane]]);
+        const float t0 = fminf(thr0, a.seed[qsv[lane]]);
+        qc[lane * QP + DIM] = t0;
+        thrv[lane] = cell_test_thr(t0);
         // the data position a candidate must not equal (none for R x S)
         qc[lane * QP + DIM + 1] = __uint_as_float(a.self ? qsv[lane] : 0xffffffffu);
+    }
+    if constexpr (scan2_qpair(DIM, E)) {
+        // the query-pair rows; the partner of the last query of an odd
+        // count has NaN coordinates and threshold -1 (accepts nothing)
+        if (lane < ((Q + 1) & ~1)) {
+            float *pr = w.qq + (lane >> 1) * qpair_row_floats(DIM) + (lane & 1);
+            const bool real = lane < Q;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) pr[2 * k] = real ? qc[lane * QP + k] : __int_as_float(0x7fc00000);
+            pr[2 * DIM] = real ? qc[lane * QP + DIM] : -1.0f;
+            pr[2 * DIM + 2] = real ? qc[lane * QP + DIM + 1] : __uint_as_float(0xffffffffu);
+        }
     }
     __syncwarp();
 
     KNN_PT(0);
+    const uint32_t qmask = Q >= 32 ? ~0u : (1u << Q) - 1u;  // the item's queries
     // a7 + a8
     for (int ob = 0; ob < NOFF; ob += 32) {
         const int o = ob + lane;
@@ -822,35 +909,33 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
         uint32_t cmask = 0;
         if (len) {
             // lower bounds of all QM queries at once: the rows of this
-            // cell's digits, read as vectors, summed rounding down
-            float lb[QM];
+            // cell's digits, read as vectors, summed rounding down, two
+            // queries per packed add (each half rounds as __fadd_rd)
+            unsigned long long lb2[QM / 2];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                const float4 *row = (const float4 *)(gsq + goff[k] * QM);
+                const ulonglong2 *row = (const ulonglong2 *)(gsq + goff[k] * QM);
 #pragma unroll
                 for (int v = 0; v < QM / 4; ++v) {
-                    const float4 t = row[v];
-                    if (k == 0) {
-                        lb[4 * v] = t.x;
-                        lb[4 * v + 1] = t.y;
-                        lb[4 * v + 2] = t.z;
-                        lb[4 * v + 3] = t.w;
-                    } else {
-                        lb[4 * v] = __fadd_rd(lb[4 * v], t.x);
-                        lb[4 * v + 1] = __fadd_rd(lb[4 * v + 1], t.y);
-                        lb[4 * v + 2] = __fadd_rd(lb[4 * v + 2], t.z);
-                        lb[4 * v + 3] = __fadd_rd(lb[4 * v + 3], t.w);
-                    }
+                    const ulonglong2 t = row[v];
+                    lb2[2 * v] = k == 0 ? t.x : f32x2_add_rd(lb2[2 * v], t.x);
+                    lb2[2 * v + 1] = k == 0 ? t.y : f32x2_add_rd(lb2[2 * v + 1], t.y);
                 }
             }
+            // against the cell-test bounds (lanes past the item's queries
+            // hold stale values: masked off below)
 #pragma unroll
             for (int v = 0; v < QM / 4; ++v) {
                 const float4 t = ((const float4 *)thrv)[v];
-                const float th[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (4 * v + j < Q && !(lb[4 * v + j] > th[j] * (1.0f + 0x1p-19f))) cmask |= 1u << (4 * v + j);
+                float l0, l1, l2, l3;
+                f32x2_unpack(lb2[2 * v], l0, l1);
+                f32x2_unpack(lb2[2 * v + 1], l2, l3);
+                if (!(l0 > t.x)) cmask |= 1u << (4 * v);
+                if (!(l1 > t.y)) cmask |= 1u << (4 * v + 1);
+                if (!(l2 > t.z)) cmask |= 1u << (4 * v + 2);
+                if (!(l3 > t.w)) cmask |= 1u << (4 * v + 3);
             }
+            cmask &= qmask;
         }
         KNN_CNT(3, __popc(__ballot_sync(FULL, len != 0)));
         KNN_CNT(4, __popc(__ballot_sync(FULL, cmask != 0)));

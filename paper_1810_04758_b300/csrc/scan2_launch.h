@@ -21,20 +21,45 @@ constexpr int S2_CTA = S2_WARPS * 32;
 // position (as float bits), padded to a multiple of 4 floats (vector loads).
 __host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) & ~3; }
 
+// Smallest d whose tiles score the item's queries two at a time (packed
+// FP32: one 64-bit register holds a coordinate of queries 2p and 2p + 1),
+// with the 64-entry buffers of K <= 32 (16 queries per item).  Measured on
+// 2M-point sets: 4% faster at d = 6, 7-8% slower at d = 4 and with the
+// 8-query items of larger buffers, slower at d = 2.
+#ifndef S2_QPAIR_DIM
+#define S2_QPAIR_DIM 6
+#endif
+__host__ __device__ constexpr bool scan2_qpair(int d, int E) { return d >= S2_QPAIR_DIM && E <= 2; }
+
+// Row of a query pair in shared memory (scan2_qpair): per dimension the
+// coordinates of queries 2p and 2p + 1 side by side, then their thresholds,
+// then their sorted positions, padded to a multiple of 4 floats.
+__host__ __device__ constexpr int qpair_row_floats(int d) { return (2 * (d + 2) + 3) & ~3; }
+__host__ __device__ constexpr int qpair_floats(int d, int QM, int E)
+{
+    return scan2_qpair(d, E) ? (QM / 2) * qpair_row_floats(d) : 0;
+}
+
+// Entries of the per-warp histogram: the radix select of buffers of more
+// than 64 entries needs 256 bins; the exact tail parks one id per buffer
+// slot there.
+__host__ __device__ constexpr int hist_entries(int E) { return E <= 2 ? 32 * E : 256; }
+
 // Entries of the per-item table of neighbour key parts (even, so that what
 // follows stays 16-byte aligned).
 __host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; }
 
 // Bytes of one warp's shared memory in k_scan2 (16-byte multiple):
 // candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
-// [QM][QP] f32, thresholds [QM] f32, counts and sorted positions [QM] x 2,
-// radix histogram [256], squared face gaps [3d][QM] f32, certificate radii
-// [QM] f32, the item's cell and the level's extent [2d] i32.
+// [QM][QP] f32, query-pair rows [QM/2][QQ] f32 (scan2_qpair), cell-test
+// thresholds [QM] f32, counts and sorted positions [QM] x 2, histogram
+// [hist_entries(E)], squared face gaps [3d][QM] f32, certificate radii [QM]
+// f32, the item's cell and the level's extent [2d] i32.
 __host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
 {
     return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
-            (size_t)QM * 4 + (size_t)QM * 8 + 256 * 4 + (size_t)QM * 3 * d * 4 + (size_t)QM * 4 +
-            (size_t)2 * d * 4 + 15) &
+            (size_t)qpair_floats(d, QM, E) * 4 + (size_t)QM * 4 + (size_t)QM * 8 + (size_t)hist_entries(E) * 4 +
+            (size_t)QM * 3 * d * 4 + (size_t)QM * 4 + (size_t)2 * d * 4 + 15) &
            ~(size_t)15;
 }
 

@@ -174,3 +174,49 @@ def test_allocator_hook_failure_is_reported(kj):
         kj.knnjoin_destroy(ctx)
         torch.cuda.synchronize()
     assert not state["live"], "every hook allocation was freed"
+
+
+def test_allocator_hook_misaligned_pointer_is_rejected(kj):
+    """A hook pointer that is not 16-byte aligned (scratch is read with
+    16-byte vector loads) is handed back to the free hook and the call fails
+    with KNN_ERR_INVALID before any kernel touches it; an aligned hook then
+    works on the same context."""
+    import torch
+    state = {"shift": 4, "live": {}, "freed_bad": 0}
+
+    def alloc(nbytes, user):
+        base = torch.cuda.caching_allocator_alloc(nbytes + 256, 0)
+        ptr = base + state["shift"]
+        state["live"][ptr] = base
+        return ptr
+
+    def free(ptr, user):
+        if ptr % 16:
+            state["freed_bad"] += 1
+        torch.cuda.caching_allocator_delete(state["live"].pop(ptr))
+
+    a_cb, f_cb = ALLOC(alloc), FREE(free)
+    cfg = kj.KnnjoinConfig()
+    cfg.device = 0
+    cfg.stream = torch.cuda.current_stream().cuda_stream
+    cfg.alloc = ctypes.cast(a_cb, ctypes.c_void_p)
+    cfg.free = ctypes.cast(f_cb, ctypes.c_void_p)
+    ctx = kj.knnjoin_create(cfg)
+    try:
+        p = gen.make_points("uniform", 5000, 3, seed=19)
+        t = torch.from_numpy(p).cuda()
+        ids = torch.empty((5000, 8), dtype=torch.int32, device="cuda")
+        dist = torch.empty((5000, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(kj.KnnJoinError) as e:
+            kj.knnjoin_self_join(ctx, t.data_ptr(), 5000, 3, 8, ids.data_ptr(), dist.data_ptr())
+        assert e.value.status == kj.KNN_ERR_INVALID
+        assert "aligned" in str(e.value)
+        assert state["freed_bad"] >= 1
+        state["shift"] = 0
+        kj.knnjoin_self_join(ctx, t.data_ptr(), 5000, 3, 8, ids.data_ptr(), dist.data_ptr())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ids.cpu().numpy(), oracle.bf(p, 8)[0])
+    finally:
+        kj.knnjoin_destroy(ctx)
+        torch.cuda.synchronize()
+    assert not state["live"]
