@@ -76,6 +76,12 @@ namespace knn {
 #ifndef S2_MIN_CTAS
 #define S2_MIN_CTAS 5
 #endif
+// The same for the instances with 128- or 256-entry buffers.  5 spills a
+// few registers there; 4 (no spills) was measured 4-9% slower on the 2M
+// exponential sets: the fifth CTA's warps hide more latency.
+#ifndef S2_MIN_CTAS_BIG
+#define S2_MIN_CTAS_BIG 5
+#endif
 
 // Start-threshold prefilter of a pass, in units of the squared certificate
 // radius (0: none).
@@ -1261,7 +1267,7 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
 
 // The scan of one join: warps take work items from the join's queue.
 template <int DIM, int QM, int E, bool MEGA>
-__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(const __grid_constant__ ScanArgs a)
+__global__ void __launch_bounds__(S2_CTA, E <= 2 ? S2_MIN_CTAS : S2_MIN_CTAS_BIG) k_scan2(const __grid_constant__ ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1285,7 +1291,7 @@ __global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2(const __grid_cons
 // << 24 | item), and the joins' arguments sit in the launch's parameter space
 // (indexed by job; a warp reads the arguments of the job it works on).
 template <int DIM, int QM, int E, bool MEGA>
-__global__ void __launch_bounds__(S2_CTA, S2_MIN_CTAS) k_scan2_multi(const __grid_constant__ MultiScanArgs p)
+__global__ void __launch_bounds__(S2_CTA, E <= 2 ? S2_MIN_CTAS : S2_MIN_CTAS_BIG) k_scan2_multi(const __grid_constant__ MultiScanArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

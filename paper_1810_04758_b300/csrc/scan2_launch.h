@@ -23,13 +23,17 @@ __host__ __device__ constexpr int query_row_floats(int d) { return (d + 2 + 3) &
 
 // Smallest d whose tiles score the item's queries two at a time (packed
 // FP32: one 64-bit register holds a coordinate of queries 2p and 2p + 1),
-// with the 64-entry buffers of K <= 32 (16 queries per item).  Measured on
-// 2M-point sets: 4% faster at d = 6, 7-8% slower at d = 4 and with the
-// 8-query items of larger buffers, slower at d = 2.
+// with buffers of at most 32 * S2_QPAIR_MAXE entries.  Measured on 2M-point
+// sets: 4% faster at d = 6 with the 64-entry buffers of K <= 32 (16 queries
+// per item), 7-8% slower at d = 4 and 7-12% slower with the 8-query items of
+// larger buffers, slower at d = 2.
 #ifndef S2_QPAIR_DIM
 #define S2_QPAIR_DIM 6
 #endif
-__host__ __device__ constexpr bool scan2_qpair(int d, int E) { return d >= S2_QPAIR_DIM && E <= 2; }
+#ifndef S2_QPAIR_MAXE
+#define S2_QPAIR_MAXE 2
+#endif
+__host__ __device__ constexpr bool scan2_qpair(int d, int E) { return d >= S2_QPAIR_DIM && E <= S2_QPAIR_MAXE; }
 
 // Row of a query pair in shared memory (scan2_qpair): per dimension the
 // coordinates of queries 2p and 2p + 1 side by side, then their thresholds,
