@@ -359,6 +359,31 @@ knnjoin_status knnjoin_self_join_noalloc(const float *points, int64_t n, int d, 
 knnjoin_status knnjoin_work_queue(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int64_t *out_sizes,
                                   int64_t cap, int64_t *out_len);
 
+/* Diagnostic: the grid index of a self-join as the join builds it (steps
+ * a3-a5: Sec. 3.1 grid index, Sec. 4.6 GPU indexing).  Runs steps a1-a5 for
+ * points (host or device, [n][d]; size rules as knnjoin_self_join), then
+ * fills the host buffers given (each may be NULL):
+ *   keys  uint64 [n]: the Morton keys of the points' level-0 cells (bit b of
+ *         cell coordinate k at key bit b*d + k), in sorted order;
+ *   perm  uint32 [n]: the original index of each sorted position (the sort
+ *         is stable: equal keys keep their original order);
+ *   grid  double [3 + 2d]: the level-0 cell side w0, the key bits per
+ *         dimension, the face origin lo[k] and the largest cell index
+ *         cmax0[k] per dimension (cell c of dimension k spans
+ *         [fl32(c w0 + lo[k]), fl32((c + 1) w0 + lo[k])), clamped to
+ *         [0, cmax0[k]]), and the kind of level `level`'s cell table
+ *         (1 dense, 0 hash map, -1 when nprobe = 0 and no table was built);
+ *   probe_runs uint32 [nprobe][2]: for each of the nprobe level-`level` cell
+ *         keys in probe_keys (uint64, host; the level-0 key shifted right by
+ *         d * level), the run [begin, end) of sorted positions that the cell
+ *         table the scan uses at that level returns -- (0, 0) for a cell
+ *         without points or beyond the level's grid.
+ * KNN_ERR_INVALID for level outside [0, key bits per dimension], device
+ * pointers for the dump's buffers, or probe arguments given by halves. */
+knnjoin_status knnjoin_index_dump(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int level,
+                                  uint64_t *keys, uint32_t *perm, double *grid, const uint64_t *probe_keys,
+                                  int64_t nprobe, uint32_t *probe_runs);
+
 /* Library version string. */
 const char *knnjoin_version(void);
 

@@ -35,7 +35,7 @@ EXPORTS = ("knnjoin_create", "knnjoin_destroy", "knnjoin_self_join", "knnjoin_jo
            "knnjoin_last_error", "knnjoin_version", "knnjoin_self_join_noalloc",
            "knnjoin_fp32_mismatch", "knnjoin_index_create", "knnjoin_index_query",
            "knnjoin_index_stats", "knnjoin_index_destroy", "knnjoin_self_join_rows",
-           "knnjoin_shard_bounds", "knnjoin_self_join_range", "knnjoin_work_queue")
+           "knnjoin_shard_bounds", "knnjoin_self_join_range", "knnjoin_work_queue", "knnjoin_index_dump")
 KNN_NOALLOC_MAX_POINTS = 65536
 
 
@@ -124,6 +124,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.knnjoin_self_join_range.restype = I
     lib.knnjoin_work_queue.argtypes = [P, P, I64, I, I, P, I64, ctypes.POINTER(ctypes.c_int64)]
     lib.knnjoin_work_queue.restype = I
+    lib.knnjoin_index_dump.argtypes = [P, P, I64, I, I, I, P, P, P, P, I64, P]
+    lib.knnjoin_index_dump.restype = I
     lib.knnjoin_index_create.argtypes = [P, P, I64, I, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.knnjoin_index_create.restype = I
     lib.knnjoin_index_query.argtypes = [P, P, I64, I, P, P]
@@ -227,6 +229,25 @@ def knnjoin_self_join_range(ctx: int, points: int, n: int, d: int, K: int, pos_b
                             out_rows: int, out_ids: int, out_dist: int) -> int:
     return _check(ctx, load_library().knnjoin_self_join_range(ctx, points, n, d, K, pos_begin, pos_end, out_rows,
                                                               out_ids, out_dist))
+
+
+def knnjoin_index_dump(ctx: int, points: int, n: int, d: int, K: int, level: int = 0, probe_keys=None):
+    """The join's grid index: (sorted keys uint64 [n], permutation uint32 [n],
+    grid dict, probe runs uint32 [m, 2] or None) -- see knnjoin_index_dump in
+    include/knnjoin.h."""
+    import numpy as np
+    keys = np.zeros(n, np.uint64)
+    perm = np.zeros(n, np.uint32)
+    grid = np.zeros(3 + 2 * d, np.float64)
+    pk = None if probe_keys is None else np.ascontiguousarray(probe_keys, dtype=np.uint64)
+    runs = None if pk is None else np.zeros((len(pk), 2), np.uint32)
+    m = 0 if pk is None else len(pk)
+    _check(ctx, load_library().knnjoin_index_dump(ctx, points, n, d, K, level, keys.ctypes.data, perm.ctypes.data,
+                                                  grid.ctypes.data, None if pk is None else pk.ctypes.data, m,
+                                                  None if runs is None else runs.ctypes.data))
+    g = {"w0": grid[0], "bits": int(grid[1]), "lo": grid[2:2 + d].copy(),
+         "cmax0": grid[2 + d:2 + 2 * d].astype(np.int64), "dense_table": int(grid[2 + 2 * d])}
+    return keys, perm, g, runs
 
 
 def knnjoin_work_queue(ctx: int, points: int, n: int, d: int, K: int):

@@ -867,6 +867,31 @@ __global__ void k_query_costs(const uint32_t *__restrict__ lvl, int64_t n, int K
     }
 }
 
+// Diagnostic (knnjoin_index_dump): the run [begin, end) of sorted positions
+// that a level's cell table gives for each probe key (the Morton bits of a
+// level cell's coordinates, nbits per dimension), as the scan looks cells up:
+// the dense table at index sum_k c_k stride_k, or the hash map at the key;
+// (0, 0) for a key beyond the level's grid or a cell without points.
+__global__ void k_probe_cells(const uint64_t *__restrict__ probe, int64_t m, int d, int nbits, DenseDims stride,
+                              DenseDims cmaxL, const uint2 *__restrict__ dense, const uint4 *__restrict__ slot,
+                              uint32_t hmask, uint2 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = probe[i];
+        int c[MAX_DIM];
+        morton_decode(key, d, nbits, c);
+        bool in = nbits * d >= 64 || (key >> (nbits * d)) == 0;
+        uint32_t idx = 0;
+        for (int k = 0; k < d; ++k) {
+            in = in && (uint32_t)c[k] <= cmaxL.stride[k];
+            idx += (uint32_t)c[k] * stride.stride[k];
+        }
+        uint2 r = make_uint2(0, 0);
+        if (in) r = dense ? dense[idx] : hash_lookup(slot, hmask, key);
+        out[i] = r;
+    }
+}
+
 // Smallest and largest value of a uint32 array (out[0] min, out[1] max,
 // initialised to ~0 and 0).
 __global__ void k_minmax_u32(const uint32_t *__restrict__ v, int64_t n, uint32_t *out)

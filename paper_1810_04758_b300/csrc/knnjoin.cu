@@ -400,6 +400,41 @@ struct Pipeline {
         }
     }
 
+    // a5: the cell table of level L over the n sorted keys -- the runs of
+    // equal key >> d L, each cell's [begin, end) of sorted positions.  A
+    // level whose grid has at most max(2n, 2^16) cells gets a dense table
+    // (one load per neighbour lookup, no host readback here), any other a
+    // hash map of 16-byte slots.  flags, rid, cbegin: n-entry scratch;
+    // small[0] receives the cell count.
+    LevelTab cell_table(const uint64_t *keys, int64_t n, int d, int L, const GridParams &hp, uint32_t *flags,
+                        uint32_t *rid, uint32_t *cbegin, uint32_t *small)
+    {
+        const int shift = d * L;
+        k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
+        scan(flags, rid, n);
+        k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
+        DenseDims dd{};
+        double G = 1.0;
+        for (int k = 0; k < d; ++k) {
+            dd.stride[k] = (uint32_t)G;
+            G *= (double)((hp.cmax0[k] >> L) + 1);
+        }
+        if (G <= std::max(2.0 * (double)n, 65536.0)) {
+            uint2 *tab = sc.get<uint2>("dense" + std::to_string(L), (size_t)G);
+            CK(cudaMemsetAsync(tab, 0, sizeof(uint2) * (size_t)G, s));
+            k_dense_insert<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, d, hp.bits - L, dd,
+                                                                  tab); ++launches;
+            return {nullptr, 0, true, tab};
+        }
+        uint32_t ncells = read1(small + 0);
+        uint32_t H = 1;
+        while (H < 2 * ncells) H <<= 1;
+        uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
+        CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
+        k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
+        return {slot, H - 1, true, nullptr};
+    }
+
     template <class K>
     void radix_sort(K *&keys, uint32_t *&vals, K *&kalt, uint32_t *&valt, int64_t n, int bits)
     {
@@ -448,6 +483,58 @@ struct Pipeline {
 
     // cut points of nshards cost-balanced ranges of sorted query positions
     // (bounds[0] = 0 .. bounds[nshards] = n) and each range's estimated cost
+    // Diagnostic (knnjoin_index_dump): index the points (a1-a5) as a join
+    // does, copy the sorted keys, the permutation and the grid to the host,
+    // build level L's cell table as the scan would, and look up the probe keys
+    // in it.
+    void index_dump(const float *pts, int64_t n, int d, int K, int L, uint64_t *keys_out, uint32_t *perm_out,
+                    double *grid_out, const uint64_t *probe, int64_t nprobe, uint32_t *runs_out)
+    {
+        const int saved_mode = res_mode;
+        res_mode = 1;
+        try {
+            run(pts, n, d, K, nullptr, nullptr);
+        } catch (...) {
+            res_mode = saved_mode;
+            throw;
+        }
+        res_mode = saved_mode;
+        const GridParams hp = res_hp;
+        if (L < 0 || L > hp.bits) fail(KNN_ERR_INVALID, "level must be in [0, bits per dimension]");
+        if (keys_out) CK(cudaMemcpyAsync(keys_out, res_keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
+        if (perm_out) CK(cudaMemcpyAsync(perm_out, res_perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
+        if (grid_out) {
+            grid_out[0] = hp.w0;
+            grid_out[1] = hp.bits;
+            grid_out[2 + 2 * d] = -1.0;  // no table built (no probes)
+            for (int k = 0; k < d; ++k) {
+                grid_out[2 + k] = hp.lo[k];
+                grid_out[2 + d + k] = hp.cmax0[k];
+            }
+        }
+        if (nprobe > 0) {
+            uint32_t *flags = sc.get<uint32_t>("flags", n), *rid = sc.get<uint32_t>("rid", n);
+            uint32_t *cbegin = sc.get<uint32_t>("cbegin", n + 1), *small = sc.get<uint32_t>("small", 16);
+            const LevelTab t = cell_table(res_keys, n, d, L, hp, flags, rid, cbegin, small);
+            if (grid_out) grid_out[2 + 2 * d] = t.dense ? 1.0 : 0.0;
+            DenseDims stride{}, cm{};
+            uint32_t G = 1;
+            for (int k = 0; k < d; ++k) {
+                stride.stride[k] = G;
+                cm.stride[k] = (uint32_t)(hp.cmax0[k] >> L);
+                G *= cm.stride[k] + 1u;  // only used with a dense table (G within 32 bits)
+            }
+            uint64_t *pk = sc.get<uint64_t>("probe_keys", (size_t)nprobe);
+            uint2 *pr = sc.get<uint2>("probe_runs", (size_t)nprobe);
+            CK(cudaMemcpyAsync(pk, probe, sizeof(uint64_t) * nprobe, cudaMemcpyHostToDevice, s));
+            k_probe_cells<<<grid_for(nprobe, 256, nsm), 256, 0, s>>>(pk, nprobe, d, hp.bits - L, stride, cm, t.dense,
+                                                                      t.slot, t.mask, pr); ++launches;
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(runs_out, pr, sizeof(uint2) * nprobe, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+
     void shard_bounds(const float *pts, int64_t n, int d, int K, int nshards, int64_t *bounds, double *costs);
 };
 
@@ -993,34 +1080,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         LevelTab local_tabs[MAX_LEVELS];
         LevelTab *tabs = rmode == 2 ? res_tabs : local_tabs;
         auto build_level = [&](int L) {
-            if (tabs[L].built) return;
-            const int shift = d * L;
-            k_run_flags<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, nullptr, n, shift, flags); ++launches;
-            scan(flags, rid, n);
-            k_run_begin<<<grid_for(n, 256, nsm), 256, 0, s>>>(flags, rid, n, cbegin, small + 0); ++launches;
-            // a level whose grid has at most max(2n, 2^16) cells gets a dense
-            // table (one load per neighbour lookup, no host readback here)
-            DenseDims dd{};
-            double G = 1.0;
-            for (int k = 0; k < d; ++k) {
-                dd.stride[k] = (uint32_t)G;
-                G *= (double)((hp.cmax0[k] >> L) + 1);
-            }
-            if (G <= std::max(2.0 * (double)n, 65536.0)) {
-                uint2 *tab = sc.get<uint2>("dense" + std::to_string(L), (size_t)G);
-                CK(cudaMemsetAsync(tab, 0, sizeof(uint2) * (size_t)G, s));
-                k_dense_insert<<<grid_for(n, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, d, hp.bits - L,
-                                                                      dd, tab); ++launches;
-                tabs[L] = {nullptr, 0, true, tab};
-                return;
-            }
-            uint32_t ncells = read1(small + 0);
-            uint32_t H = 1;
-            while (H < 2 * ncells) H <<= 1;
-            uint4 *slot = sc.get<uint4>("hslot" + std::to_string(L), H);
-            CK(cudaMemsetAsync(slot, 0xff, sizeof(uint4) * H, s));
-            k_hash_insert<<<grid_for(ncells, 256, nsm), 256, 0, s>>>(keys, cbegin, small + 0, shift, slot, H - 1); ++launches;
-            tabs[L] = {slot, H - 1, true, nullptr};
+            if (!tabs[L].built) tabs[L] = cell_table(keys, n, d, L, hp, flags, rid, cbegin, small);
         };
 
         // work items of a (level, position)-ordered list of sorted positions
@@ -1929,6 +1989,23 @@ knnjoin_status knnjoin_shard_bounds(knnjoin_ctx *ctx, const float *points, int64
         ctx->main.shard_bounds(points, n, d, K, nshards, b.data(), cs.data());
         memcpy(bounds, b.data(), sizeof(int64_t) * (nshards + 1));
         if (costs) memcpy(costs, cs.data(), sizeof(double) * nshards);
+    });
+}
+
+knnjoin_status knnjoin_index_dump(knnjoin_ctx *ctx, const float *points, int64_t n, int d, int K, int level,
+                                  uint64_t *keys, uint32_t *perm, double *grid, const uint64_t *probe_keys,
+                                  int64_t nprobe, uint32_t *probe_runs)
+{
+    if (!ctx) return KNN_ERR_INVALID;
+    return guard(ctx, [&] {
+        if (!points) fail(KNN_ERR_INVALID, "NULL pointer argument");
+        validate_sizes(n, d, K);
+        if (nprobe < 0 || (nprobe > 0 && (!probe_keys || !probe_runs)))
+            fail(KNN_ERR_INVALID, "probe keys and runs must be given together (nprobe >= 0)");
+        if ((keys && is_device_ptr(keys)) || (perm && is_device_ptr(perm)) || (grid && is_device_ptr(grid)) ||
+            (nprobe > 0 && (is_device_ptr(probe_keys) || is_device_ptr(probe_runs))))
+            fail(KNN_ERR_INVALID, "the dump's buffers must be host memory");
+        ctx->main.index_dump(points, n, d, K, level, keys, perm, grid, probe_keys, nprobe, probe_runs);
     });
 }
 
