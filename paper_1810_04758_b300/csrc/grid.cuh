@@ -9,10 +9,11 @@
 //                    reaches K per sampled point; cell side, grid, key bits.
 //  a3  k_keys        exact level-0 cell of every point, Morton key.
 //  a4  radix sort (primitives.cuh).
-//  a5  k_gather      coordinates permuted to key order (SoA).
-//      k_run_flags / k_cells / k_hash_insert: the non-empty cells of a level
-//                    (a level-l cell is a run of equal key >> (d*l)) and a
-//                    hash map from cell key to its run.
+//  a5  k_gather      coordinates permuted to key order (padded AoS rows).
+//      k_run_flags / k_run_begin / k_dense_insert / k_hash_insert: the
+//                    non-empty cells of a level (a level-l cell is a run of
+//                    equal key >> (d*l)) and a dense table or a hash map from
+//                    cell to its run.
 //  a6  k_group_*     density-ordered work queue: groups of queries sharing a
 //                    cell, sorted by count descending (Fig. 4), split into
 //                    work items.

@@ -4,16 +4,16 @@
 // Each warp works alone (no block barriers) on work items of up to QM
 // queries that share a level-l grid cell.  Per batch of 32 neighbour cells,
 // nearest first:
-//   a7  each lane forms its cell's level key from the item's table of
-//       dilated coordinate parts, probes the level's hash map (one 16-byte
+//   a7  each lane forms its cell's key (or dense-table index) from the
+//       item's table of coordinate parts, reads the level's cell table (one
 //       load per probe) and, for every query of the item, tests the cell's
 //       box against the query's threshold with a rounded-down squared
 //       distance (a bit per query: the cell mask); a warp prefix sum
 //       flattens the runs;
 //   a8  runs of at least S2_BIG points go first, in super-tiles of S2_SUPER
 //       consecutive sorted points, each tested per query against the box of
-//       its Morton prefix (groups of S2_MEGA super-tiles are tested first and
-//       skipped whole); the other runs are scanned two tiles at a time:
+//       its Morton prefix (on skewed data S2_MEGA super-tiles at once, one
+//       per lane); the other runs are scanned two tiles at a time:
 //       lane t holds candidates t and t + 32, loads their coordinates once
 //       and scores them against every query in the tiles' masks (query rows
 //       broadcast from shared memory), so a candidate read serves up to QM
@@ -22,8 +22,8 @@
 //       distance to the faces of the scanned box, beyond which no point can
 //       belong to a certified answer -- or the band of the K-th value an
 //       earlier pass found, and T (1 + 2^-15) + 2^-120 once the per-query
-//       buffer of B entries has filled (T = its K-th value, by a warp radix
-//       select);
+//       buffer of B entries has filled (T = its K-th value, by a warp sort
+//       or radix select);
 //   a9  per query, the warp sorts the buffer as 32-bit keys, takes T32 (the
 //       K-th FP32 value), keeps the band d2_32 <= T32 (1 + 2^-15) + 2^-120,
 //       scores it with the bit-exact canonical FP64 distance (exact.cuh),
