@@ -272,6 +272,20 @@ def oracle_full_join(name: str, threads: int):
     return time.perf_counter() - t0
 
 
+def oracle_bf_small(threads: int) -> dict:
+    """The brute-force oracle on the small uniform set (Unif-2D, n = 20,000,
+    K = 8) with all host cores and with one: query points/s of each."""
+    import oracle
+    p, K = gen.config_points("unif2d_20k")
+    out = {"set": "unif2d_20k (n=20000, d=2, K=8)", "what": "oracle_bf: every pair, canonical FP64"}
+    for label, th in (("all_cores", threads), ("one_core", 1)):
+        t0 = time.perf_counter()
+        oracle.bf(p, K, threads=th)
+        dt = time.perf_counter() - t0
+        out[label] = {"threads": th, "s": round(dt, 3), "q_per_s": len(p) / dt}
+    return out
+
+
 def step_config(args, world: int) -> dict:
     """The `config` of the unif / expo step (both arms print the same)."""
     return {"workload": WORKLOAD_TEXT[args.workload], "n": 2_000_000, "d": [2, 4, 6],
@@ -596,7 +610,8 @@ def run_ours(args, rank, world, local_rank):
                "detail": detail,
                "full_join": {"set": full_name, "rows": len(hosts[full_name][0]), "s": round(full_s, 3),
                              "q_per_s": len(hosts[full_name][0]) / full_s,
-                             "what": "one whole oracle join of this set, all rows, measured"}}
+                             "what": "one whole oracle join of this set, all rows, measured"},
+               "brute_force_small": oracle_bf_small(cores)}
 
     ctx.close()
     if rank != 0:
