@@ -43,6 +43,7 @@
 #include "scan.cuh"
 #include "scan2_launch.h"
 #include "diag.cuh"
+#include "tail.cuh"
 
 using namespace knn;
 
@@ -268,6 +269,40 @@ struct TuneTable {
 // One join pipeline (stream + scratch + pinned readback).
 // ---------------------------------------------------------------------------
 // Hash map from the cell keys of one grid level to their runs of points.
+// Brute-force tail (tail.cuh) for dimension DIM: four radix-select rounds,
+// the band collection and the per-query finish, on stream s.
+template <int DIM>
+void tail_launch_dim(const TailArgs &t, int64_t chunk, unsigned chunks, cudaStream_t s, int64_t &launches)
+{
+    const dim3 g(chunks, (unsigned)t.m);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        k_tail_hist<DIM><<<g, 256, 0, s>>>(t, shift, chunk); ++launches;
+        k_tail_select<<<t.m, 32, 0, s>>>(t, shift); ++launches;
+    }
+    k_tail_collect<DIM><<<g, 256, 0, s>>>(t, chunk); ++launches;
+    k_tail_finish<DIM><<<t.m, 32, 0, s>>>(t); ++launches;
+}
+
+void tail_launch(int d, const TailArgs &t, int64_t chunk, unsigned chunks, cudaStream_t s, int64_t &launches)
+{
+    switch (d) {
+    case 1: tail_launch_dim<1>(t, chunk, chunks, s, launches); break;
+    case 2: tail_launch_dim<2>(t, chunk, chunks, s, launches); break;
+    case 3: tail_launch_dim<3>(t, chunk, chunks, s, launches); break;
+    case 4: tail_launch_dim<4>(t, chunk, chunks, s, launches); break;
+    case 5: tail_launch_dim<5>(t, chunk, chunks, s, launches); break;
+    case 6: tail_launch_dim<6>(t, chunk, chunks, s, launches); break;
+    case 7: tail_launch_dim<7>(t, chunk, chunks, s, launches); break;
+    default: tail_launch_dim<8>(t, chunk, chunks, s, launches); break;
+    }
+}
+
+// A tail of m queries against n points goes to the brute force when
+// m * n is at most this (about 3.4 10^8 distance evaluations over its five
+// sweeps of the pairs, a fraction of a millisecond); larger tails take a
+// whole-grid scan pass.
+constexpr double TAIL_BF_PAIRS = (double)(1 << 26);
+
 struct LevelTab {
     uint4 *slot = nullptr;
     uint32_t mask = 0;
@@ -961,6 +996,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
     // doubles instead, which bounds the number of epochs).
     int pass = 0;
     int64_t cand_before = 0;
+    int64_t tail_cand = 0;  // pairs the brute-force tail evaluated
     int first_level = -1;
     uint32_t *done = nullptr;  // per original query row (paper's policy)
     if (policy == 1) {
@@ -1331,11 +1367,67 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 m = next;
                 ++pass;
                 if (m > 0 && pass >= 2 && tail_limit >= 0 && m <= tail_limit) {
-                    // the tail: the rest in one pass over the whole grid
-                    k_set_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, m, lvl, (uint32_t)hp.top_level);
-                    ++launches;
-                    next_lmin = next_lmax = (uint32_t)hp.top_level;
-                    range_known = true;
+                    if ((double)m * (double)n <= TAIL_BF_PAIRS) {
+                        // few queries left: every (query, point) pair over the
+                        // whole GPU (tail.cuh); a query whose band overflows
+                        // keeps status 2 and takes the whole-grid pass below
+                        TailArgs t{};
+                        t.xsort = xsort;
+                        t.qxsort = qxsort;
+                        t.perm = perm;
+                        t.qperm = qperm;
+                        t.list = active;
+                        t.m = (int)m;
+                        t.n = n;
+                        t.K = K;
+                        t.self = self ? 1 : 0;
+                        t.fixed_ok = hp.fixed_ok;
+                        t.F = hp.F;
+                        t.prefix = sc.get<uint32_t>("tail_prefix", (size_t)m);
+                        t.rank = sc.get<uint32_t>("tail_rank", (size_t)m);
+                        t.hist = sc.get<uint32_t>("tail_hist", (size_t)m * 256);
+                        t.cnt = sc.get<uint32_t>("tail_cnt", (size_t)m);
+                        t.band = sc.get<uint32_t>("tail_band", (size_t)m * TAIL_CAP);
+                        t.status = status;
+                        t.out_ids = ids;
+                        t.out_dist = dist;
+                        t.row0 = row0;
+                        t.out_rows = chunked ? chunk_rows : nrows;
+                        t.sorted_rows = shard_sorted ? 1 : 0;
+                        CK(cudaMemsetAsync(t.prefix, 0, sizeof(uint32_t) * m, s));
+                        CK(cudaMemsetAsync(t.hist, 0, sizeof(uint32_t) * m * 256, s));
+                        CK(cudaMemsetAsync(t.cnt, 0, sizeof(uint32_t) * m, s));
+                        k_fill_u32<<<grid_for(m, 256, nsm), 256, 0, s>>>(t.rank, m, (uint32_t)K); ++launches;
+                        // about 4 blocks per SM in all, chunks of at least 1024 points
+                        const int64_t want = std::max<int64_t>(1, (int64_t)4 * nsm / m);
+                        const int64_t chunk = std::max<int64_t>(1024, (n + want - 1) / want);
+                        const unsigned chunks = (unsigned)((n + chunk - 1) / chunk);
+                        CK(cudaEventRecord(evs[0], s));
+                        tail_launch(d, t, chunk, chunks, s, launches);
+                        CK(cudaEventRecord(evs[1], s));
+                        CK(cudaGetLastError());
+                        const int64_t left = select_list(active, m, 2, active2);
+                        float tms = 0.f;
+                        CK(cudaEventElapsedTime(&tms, evs[0], evs[1]));
+                        ms_scan += tms;
+                        const int64_t pairs = m * (n - (self ? 1 : 0));
+                        tail_cand += pairs;
+                        if (pass < 16) {
+                            stats.ms_pass[pass] = tms;
+                            stats.pass_queries[pass] = m;
+                            stats.pass_candidates[pass] = pairs;
+                        }
+                        ++pass;
+                        std::swap(active, active2);
+                        m = left;
+                    }
+                    if (m > 0) {
+                        // the tail: the rest in one pass over the whole grid
+                        k_set_levels<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, m, lvl, (uint32_t)hp.top_level);
+                        ++launches;
+                        next_lmin = next_lmax = (uint32_t)hp.top_level;
+                        range_known = true;
+                    }
                 }
             }
             if (chunked) {
@@ -1394,7 +1486,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
 #endif
     unsigned long long hs[4];
     memcpy(hs, pinned, sizeof(hs));
-    stats.candidates = (int64_t)hs[0];
+    stats.candidates = (int64_t)hs[0] + tail_cand;
     stats.overflow_queries += (int64_t)hs[1];
     stats.band_entries = (int64_t)hs[2];
     float ms = 0.f, ms1 = 0.f;

@@ -192,55 +192,6 @@ static __device__ int warp_compact_hi(uint64_t *buf, int cnt, uint32_t thr, int 
     return out;
 }
 
-__device__ __forceinline__ bool xless(uint64_t da, uint32_t ia, uint64_t db, uint32_t ib)
-{
-    return da < db || (da == db && ia < ib);
-}
-
-// Bitonic sort, ascending by (D, I), of 32*E entries held E per lane in
-// blocked order (entry g = lane*E + e).
-template <int E>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&D)[E], uint32_t (&I)[E], int lane)
-{
-    constexpr int N = 32 * E;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < E) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int p = e ^ j;
-                    if (p > e) {
-                        const int g = lane * E + e;
-                        const bool up = (g & k) == 0;
-                        const bool sw = up ? xless(D[p], I[p], D[e], I[e]) : xless(D[e], I[e], D[p], I[p]);
-                        if (sw) {
-                            uint64_t td = D[e]; D[e] = D[p]; D[p] = td;
-                            uint32_t ti = I[e]; I[e] = I[p]; I[p] = ti;
-                        }
-                    }
-                }
-            } else {
-                const int lm = j / E;
-                const bool lower = (lane & lm) == 0;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    uint64_t od = __shfl_xor_sync(FULL, D[e], lm);
-                    uint32_t oi = __shfl_xor_sync(FULL, I[e], lm);
-                    const int g = lane * E + e;
-                    const bool up = (g & k) == 0;
-                    const bool take = (lower == up) ? xless(od, oi, D[e], I[e]) : xless(D[e], I[e], od, oi);
-                    if (take) {
-                        D[e] = od;
-                        I[e] = oi;
-                    }
-                }
-            }
-        }
-    }
-}
-
 template <int DIM>
 __device__ __forceinline__ void load_query_row(const float *qc, int i, float (&q)[DIM], float &thr, uint32_t &qs)
 {
