@@ -172,7 +172,9 @@ __global__ void k_tail_finish(const TailArgs t)
     const int j = blockIdx.x, lane = threadIdx.x & 31;
     const uint32_t s = t.list[j];
     const uint32_t c = t.cnt[j];
-    if (c > (uint32_t)TAIL_CAP) {  // massive ties: a whole-grid scan pass takes it
+    // massive ties (or, should the band ever hold fewer than K, anything
+    // amiss): a whole-grid scan pass takes the query
+    if (c > (uint32_t)TAIL_CAP || c < (uint32_t)t.K) {
         if (lane == 0) t.status[s] = 2;
         return;
     }
