@@ -72,9 +72,14 @@ namespace knn {
 #define S2_WIDE_DIM 2
 #endif
 
-// Resident CTAs per SM the register allocation is sized for.
+// Resident CTAs per SM the register allocation is sized for (5: 96
+// registers a thread).  At d <= 2 the shared memory of 64-entry buffers
+// leaves room for 6 (80 registers), measured 5% faster on 2M-point 2-D sets.
 #ifndef S2_MIN_CTAS
 #define S2_MIN_CTAS 5
+#endif
+#ifndef S2_MIN_CTAS_2D
+#define S2_MIN_CTAS_2D 6
 #endif
 // The same for the instances with 128- or 256-entry buffers.  5 spills a
 // few registers there; 4 (no spills) was measured 4-9% slower on the 2M
@@ -649,7 +654,7 @@ struct Scan2Warp {
     float *thrv;     // [QM] cell-test bounds of the thresholds, contiguous (vector loads)
     int *cnt;        // [QM]
     uint32_t *qsv;   // [QM]
-    uint32_t *hist;  // [256]
+    uint32_t *hist;  // [hist_entries] (or the face-gap table: hist_aliased)
     // [3d][QM]: per dimension, the squared distance (rounded down) from each
     // query to the lower neighbour cell, 0 (same slab), to the upper one --
     // row 3k + g for the base-3 digit g of a neighbour offset in dimension k,
@@ -667,8 +672,9 @@ struct Scan2Warp {
         thrv = qq + qpair_floats(DIM, QM, E);
         cnt = (int *)(thrv + QM);
         qsv = (uint32_t *)(cnt + QM);
-        hist = qsv + QM;
-        gsq = (float *)(hist + hist_entries(E));
+        uint32_t *own_hist = qsv + QM;
+        gsq = (float *)(own_hist + hist_entries(DIM, QM, E));
+        hist = hist_aliased(DIM, QM, E) ? (uint32_t *)gsq : own_hist;
         rcert = gsq + 3 * DIM * QM;
         cellv = (int *)(rcert + QM);
     }
@@ -1218,7 +1224,8 @@ __device__ __forceinline__ void scan2_item(const ScanArgs &a, uint32_t item, con
 
 // The scan of one join: warps take work items from the join's queue.
 template <int DIM, int QM, int E, bool MEGA>
-__global__ void __launch_bounds__(S2_CTA, E <= 2 ? S2_MIN_CTAS : S2_MIN_CTAS_BIG) k_scan2(const __grid_constant__ ScanArgs a)
+__global__ void __launch_bounds__(S2_CTA, E <= 2 ? (DIM <= 2 ? S2_MIN_CTAS_2D : S2_MIN_CTAS) : S2_MIN_CTAS_BIG)
+k_scan2(const __grid_constant__ ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1242,7 +1249,8 @@ __global__ void __launch_bounds__(S2_CTA, E <= 2 ? S2_MIN_CTAS : S2_MIN_CTAS_BIG
 // << 24 | item), and the joins' arguments sit in the launch's parameter space
 // (indexed by job; a warp reads the arguments of the job it works on).
 template <int DIM, int QM, int E, bool MEGA>
-__global__ void __launch_bounds__(S2_CTA, E <= 2 ? S2_MIN_CTAS : S2_MIN_CTAS_BIG) k_scan2_multi(const __grid_constant__ MultiScanArgs p)
+__global__ void __launch_bounds__(S2_CTA, E <= 2 ? (DIM <= 2 ? S2_MIN_CTAS_2D : S2_MIN_CTAS) : S2_MIN_CTAS_BIG)
+k_scan2_multi(const __grid_constant__ MultiScanArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -46,8 +46,14 @@ __host__ __device__ constexpr int qpair_floats(int d, int QM, int E)
 
 // Entries of the per-warp histogram: the radix select of buffers of more
 // than 64 entries needs 256 bins; the exact tail parks one id per buffer
-// slot there.
-__host__ __device__ constexpr int hist_entries(int E) { return E <= 2 ? 32 * E : 256; }
+// slot there.  With 64-entry buffers the parking shares the squared face-gap
+// table instead when that is large enough (it is free once the scan is
+// done), which leaves the histogram out.
+__host__ __device__ constexpr bool hist_aliased(int d, int QM, int E) { return E <= 2 && 3 * d * QM >= 32 * E; }
+__host__ __device__ constexpr int hist_entries(int d, int QM, int E)
+{
+    return hist_aliased(d, QM, E) ? 0 : (E <= 2 ? 32 * E : 256);
+}
 
 // Entries of the per-item table of neighbour key parts (even, so that what
 // follows stays 16-byte aligned).
@@ -57,12 +63,12 @@ __host__ __device__ constexpr int dil_entries(int d) { return (3 * d + 1) & ~1; 
 // candidate buffers [QM][32E] u64, neighbour key parts [3d] u64, query rows
 // [QM][QP] f32, query-pair rows [QM/2][QQ] f32 (scan2_qpair), cell-test
 // thresholds [QM] f32, counts and sorted positions [QM] x 2, histogram
-// [hist_entries(E)], squared face gaps [3d][QM] f32, certificate radii [QM]
+// [hist_entries(d, QM, E)], squared face gaps [3d][QM] f32, certificate radii [QM]
 // f32, the item's cell and the level's extent [2d] i32.
 __host__ __device__ constexpr size_t scan2_warp_bytes(int d, int QM, int E)
 {
     return ((size_t)QM * 32 * E * 8 + (size_t)dil_entries(d) * 8 + (size_t)QM * query_row_floats(d) * 4 +
-            (size_t)qpair_floats(d, QM, E) * 4 + (size_t)QM * 4 + (size_t)QM * 8 + (size_t)hist_entries(E) * 4 +
+            (size_t)qpair_floats(d, QM, E) * 4 + (size_t)QM * 4 + (size_t)QM * 8 + (size_t)hist_entries(d, QM, E) * 4 +
             (size_t)QM * 3 * d * 4 + (size_t)QM * 4 + (size_t)2 * d * 4 + 15) &
            ~(size_t)15;
 }
