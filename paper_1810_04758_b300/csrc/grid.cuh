@@ -927,6 +927,12 @@ __global__ void k_fetch(uint32_t *dst, const uint32_t *__restrict__ src, int wor
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
 }
 
+// dst[0] = *a + *b (a list's length: the last exclusive prefix plus the last flag).
+__global__ void k_fetch_sum2(uint32_t *dst, const uint32_t *__restrict__ a, const uint32_t *__restrict__ b)
+{
+    if (threadIdx.x == 0) dst[0] = *a + *b;
+}
+
 __global__ void k_iota(uint32_t *out, int64_t m)
 {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m;

@@ -411,6 +411,21 @@ struct Pipeline {
         }
     }
 
+    // *a + *b (both device words), read back once this stream has synchronised
+    int64_t read_total(const uint32_t *a, const uint32_t *b)
+    {
+        if (pinned_dev) {
+            k_fetch_sum2<<<1, 32, 0, s>>>(pinned_dev, a, b);
+            ++launches;
+            CK(cudaStreamSynchronize(s));
+            return (int64_t)pinned[0];
+        }
+        fetch(pinned, a, 4);
+        fetch(pinned + 1, b, 4);
+        CK(cudaStreamSynchronize(s));
+        return (int64_t)pinned[0] + pinned[1];
+    }
+
     template <class T>
     T read1(const T *dev)
     {
@@ -429,7 +444,10 @@ struct Pipeline {
         int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
         uint32_t *sums = sc.get<uint32_t>("scan_sums" + std::to_string(depth), (size_t)nb + 1);
         k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, sums, m); ++launches;
-        if (nb > 1) {
+        if (nb > 1 && nb <= SCAN_TILE) {
+            // each tile adds the sum of the tiles before it, formed in place
+            k_scan_add_direct<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, sums, m); ++launches;
+        } else if (nb > 1) {
             scan(sums, sums, nb, depth + 1);
             k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, sums, m); ++launches;
         }
@@ -1147,10 +1165,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             uint32_t *nit = sc.get<uint32_t>("nit", ng), *ioff = sc.get<uint32_t>("ioff", ng);
             k_group_nitems<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, nit); ++launches;
             scan(nit, ioff, ng);
-            fetch(pinned, ioff + ng - 1, 4);
-            fetch(pinned + 1, nit + ng - 1, 4);
-            CK(cudaStreamSynchronize(s));
-            nitems = pinned[0] + pinned[1];
+            nitems = (uint32_t)read_total(ioff + ng - 1, nit + ng - 1);
             uint2 *items = sc.get<uint2>("items", nitems);
             k_group_items<<<grid_for(ng, 256, nsm), 256, 0, s>>>(gbegin, sval, small + 1, qpi, ioff, list, lvl, items); ++launches;
             return items;
@@ -1159,10 +1174,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         auto select_list = [&](const uint32_t *list, int64_t mm, uint32_t value, uint32_t *out) -> int64_t {
             k_status_flags<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, status, mm, value, flags); ++launches;
             scan(flags, rid, mm);
-            fetch(pinned, rid + mm - 1, 4);
-            fetch(pinned + 1, flags + mm - 1, 4);
-            CK(cudaStreamSynchronize(s));
-            int64_t cntv = (int64_t)pinned[0] + pinned[1];
+            const int64_t cntv = read_total(rid + mm - 1, flags + mm - 1);
             if (cntv > 0) {
                 k_compact<<<grid_for(mm, 256, nsm), 256, 0, s>>>(list, flags, rid, mm, out); ++launches;
             }
@@ -1178,10 +1190,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 // the queries not done yet, by their position in this epoch's order
                 k_undone_flags<<<grid_for(nq, 256, nsm), 256, 0, s>>>(qperm, done, nq, flags); ++launches;
                 scan(flags, rid, nq);
-                fetch(pinned, rid + nq - 1, 4);
-                fetch(pinned + 1, flags + nq - 1, 4);
-                CK(cudaStreamSynchronize(s));
-                m = (int64_t)pinned[0] + pinned[1];
+                m = read_total(rid + nq - 1, flags + nq - 1);
                 k_compact<<<grid_for(nq, 256, nsm), 256, 0, s>>>(active, flags, rid, nq, active2); ++launches;
                 std::swap(active, active2);
             }
@@ -1195,10 +1204,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 }
                 ++launches;
                 scan(flags, rid, m);
-                fetch(pinned, rid + m - 1, 4);
-                fetch(pinned + 1, flags + m - 1, 4);
-                CK(cudaStreamSynchronize(s));
-                const int64_t mr = (int64_t)pinned[0] + pinned[1];
+                const int64_t mr = read_total(rid + m - 1, flags + m - 1);
                 k_compact<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, flags, rid, m, active2); ++launches;
                 std::swap(active, active2);
                 m = mr;

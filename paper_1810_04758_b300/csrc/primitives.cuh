@@ -41,6 +41,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t *in,
     if (threadIdx.x == 0 && sums) sums[blockIdx.x] = total;
 }
 
+// Second half of a two-launch scan (nb <= SCAN_TILE tiles): block b adds
+// the exclusive prefix of the tile sums, sum of sums[0..b), which it forms
+// itself (no separate scan of the sums).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add_direct(uint32_t *out, const uint32_t *sums, int64_t n)
+{
+    __shared__ uint32_t sm[32];
+    const int b = (int)blockIdx.x;
+    uint32_t part = 0;
+    for (int i = threadIdx.x; i < b; i += SCAN_THREADS) part += sums[i];
+    uint32_t add;
+    block_exclusive_scan(part, add, sm);
+    const int64_t base = (int64_t)b * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        const int64_t idx = base + i;
+        if (idx < n) out[idx] += add;
+    }
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(uint32_t *out, const uint32_t *sums, int64_t n)
 {
     uint32_t add = sums[blockIdx.x];
