@@ -506,6 +506,24 @@ __global__ void k_bump_levels(const uint32_t *__restrict__ list, const uint32_t 
 // out[3] = the smallest / largest level of the status-1 entries, after
 // moving them one level up when `bump` is set (k_bump_levels's rule).
 // out must hold {0, 0, 0xffffffff, 0} on entry (k_summary_init).
+// Start of a pass: the device words its kernels accumulate into -- [2] the
+// largest group (work queue), [3] the scan's queue head, [4..5] the active
+// queries' level range (min, max), [8..11] the end-of-pass summary (as
+// k_summary_init) -- in one launch.
+__global__ void k_pass_init(uint32_t *small)
+{
+    if (threadIdx.x == 0) {
+        small[2] = 0u;
+        small[3] = 0u;
+        small[4] = 0xffffffffu;
+        small[5] = 0u;
+        small[8] = 0u;
+        small[9] = 0u;
+        small[10] = 0xffffffffu;
+        small[11] = 0u;
+    }
+}
+
 __global__ void k_summary_init(uint32_t *out)
 {
     if (threadIdx.x == 0) {

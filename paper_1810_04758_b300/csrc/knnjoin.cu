@@ -1143,7 +1143,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             k_run_flags_lv<<<grid_for(mm, 256, nsm), 256, 0, s>>>(qkeys, list, lvl, mm, d, flags); ++launches;
             scan(flags, rid, mm);
             k_run_begin<<<grid_for(mm, 256, nsm), 256, 0, s>>>(flags, rid, mm, gbegin, small + 1); ++launches;
-            CK(cudaMemsetAsync(small + 2, 0, 4, s));
+            // small[2] (the largest group) is zero here: set by the pass's k_pass_init
             uint32_t *skey = sc.get<uint32_t>("skey", mm), *sval = sc.get<uint32_t>("sval", mm);
             uint32_t *skey2 = sc.get<uint32_t>("skey2", mm), *sval2 = sc.get<uint32_t>("sval2", mm);
             k_group_sizes<<<grid_for(mm, 256, nsm), 256, 0, s>>>(gbegin, small + 1, skey, sval, small + 2); ++launches;
@@ -1220,8 +1220,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 if (pass > (policy == 1 ? 8192 : 4 * MAX_LEVELS)) fail(KNN_ERR_CUDA, "internal: too many passes");
                 // order the active list by level (stable: positions stay ordered
                 // within a level) and build the levels' hash maps
-                k_fill_u32<<<1, 32, 0, s>>>(small + 4, 1, 0xffffffffu); ++launches;
-                k_fill_u32<<<1, 32, 0, s>>>(small + 5, 1, 0u); ++launches;
+                k_pass_init<<<1, 32, 0, s>>>(small); ++launches;
                 k_level_keys<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, lvl, m, lkey, small + 4); ++launches;
                 uint32_t lmin = next_lmin, lmax = next_lmax;
                 if (!range_known) {
@@ -1287,7 +1286,6 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 a.active = active;
                 a.nactive = m;
                 a.nitems = nitems;
-                CK(cudaMemsetAsync(small + 3, 0, 4, s));
                 CK(cudaEventRecord(evs[0], s));
                 // skewed data, or a re-queued pass: walk long runs by
                 // mega-tiles (a query's box may hold long runs far from it)
@@ -1315,8 +1313,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                 bool counts_known = false;
                 int64_t m1 = 0;
                 if (fast) {
-                    uint32_t *summ = small + 8;
-                    k_summary_init<<<1, 32, 0, s>>>(summ); ++launches;
+                    uint32_t *summ = small + 8;  // initialised by the pass's k_pass_init
                     k_status_summary<<<grid_for(m, 256, nsm), 256, 0, s>>>(active, status, m, lvl, hp.top_level,
                                                                           policy == 0 ? 1 : 0, summ); ++launches;
                     fetch(pinned, summ, 4 * sizeof(uint32_t));
@@ -1329,6 +1326,7 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
                     if (mo > 0) {
                         // queries whose buffer overflowed (massive ties): general kernel
                         int64_t mo2 = select_list(active, m, 2, ovl);
+                        CK(cudaMemsetAsync(small + 2, 0, 4, s));  // make_items' largest group
                         a.items = make_items(ovl, mo2, SCAN_WARPS, nitems);
                         a.active = ovl;
                         a.nactive = mo2;
