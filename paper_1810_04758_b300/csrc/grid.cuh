@@ -696,6 +696,37 @@ __global__ void k_group_sizes(const uint32_t *__restrict__ gbegin, const uint32_
 }
 
 // sortkey = maxsize - size (ascending sort => size descending, stable)
+// The order of at most GROUP_SORT_SMALL groups by size descending, ties by
+// group index (what the radix sort of the size keys gives, it being stable),
+// in one block: a bitonic sort in shared memory of (max - size) << 12 | g.
+constexpr int GROUP_SORT_SMALL = 4096;
+__global__ void __launch_bounds__(1024) k_group_sort_small(const uint32_t *__restrict__ sizes, const uint32_t *ng_p,
+                                                         const uint32_t *maxsize, uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t v[GROUP_SORT_SMALL];
+    const uint32_t ng = *ng_p, mx = *maxsize;
+    uint32_t N = 64;
+    while (N < ng) N <<= 1;
+    for (uint32_t g = threadIdx.x; g < N; g += blockDim.x)
+        v[g] = g < ng ? ((mx - sizes[g]) << 12) | g : 0xffffffffu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                const uint32_t i = 2 * t - (t & (j - 1)), p = i + j;  // i has bit j clear
+                const bool up = (i & k) == 0;
+                const uint32_t a = v[i], b = v[p];
+                if ((a > b) == up) {
+                    v[i] = b;
+                    v[p] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) order[g] = v[g] & 4095u;
+}
+
 __global__ void k_group_sortkey(uint32_t *__restrict__ sortkey, const uint32_t *ng_p, const uint32_t *maxsize)
 {
     uint32_t ng = *ng_p, mx = *maxsize;

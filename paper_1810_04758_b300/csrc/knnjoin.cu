@@ -1150,8 +1150,14 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
             fetch(pinned, small + 1, 8);
             CK(cudaStreamSynchronize(s));
             uint32_t ng = pinned[0], maxsz = pinned[1];
-            k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
-            radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+            if (ng <= (uint32_t)GROUP_SORT_SMALL && bitlen32(maxsz) <= 20) {
+                // few groups: one block sorts them (one launch instead of the
+                // radix sort's three or more per digit)
+                k_group_sort_small<<<1, 1024, 0, s>>>(skey, small + 1, small + 2, sval); ++launches;
+            } else {
+                k_group_sortkey<<<grid_for(ng, 256, nsm), 256, 0, s>>>(skey, small + 1, small + 2); ++launches;
+                radix_sort<uint32_t>(skey, sval, skey2, sval2, ng, bitlen32(maxsz));
+            }
             if (queue_out && queue_out->empty()) {
                 std::vector<uint32_t> hg(ng + 1), hs(ng);
                 CK(cudaMemcpyAsync(hg.data(), gbegin, sizeof(uint32_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
