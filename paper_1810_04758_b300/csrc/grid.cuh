@@ -166,6 +166,79 @@ __device__ __forceinline__ void sample_slice(int64_t S, int64_t &i0, int64_t &i1
     i1 = min(S, i0 + per);
 }
 
+struct ParamsIn {
+    int64_t n;
+    int d, K;
+    int64_t S, m;        // histogram samples / subset size
+    float width_mult;    // cell side = width_mult * eps_min
+    int start_level;
+    int max_finer;       // cap on levels finer than the search-distance width
+};
+
+__device__ __forceinline__ float eps_mean_of(const PrepReduce *red)
+{
+    return red->eps_pairs ? (float)(red->eps_sum / (double)red->eps_pairs) : 0.0f;
+}
+
+// Stage 0 of the grid parameters (written by one thread): the grid-independent
+// fields, from the reductions of k_prep and k_eps_pairs.
+__device__ void params_stage0(const PrepReduce *red, const ParamsIn &in, GridParams *gp)
+{
+    const int d = in.d;
+    gp->n = (int)in.n;
+    gp->d = d;
+    gp->K = in.K;
+    gp->nonfinite = red->nonfinite;
+    for (int k = 0; k < d; ++k) {
+        gp->lo[k] = fdec(red->lo_enc[k]);
+        gp->hi[k] = fdec(red->hi_enc[k]);
+    }
+    if (red->max_msb < red->min_lsb) {  // every coordinate is zero
+        gp->fixed_ok = 1;
+        gp->F = 0;
+    } else {
+        int F = -red->min_lsb;
+        gp->F = F;
+        gp->fixed_ok = (red->max_msb + F <= 29) ? 1 : 0;
+    }
+    gp->eps_mean = eps_mean_of(red);
+    gp->eps_min = 0.0f;
+}
+
+// The search distance of a histogram h of bins range / 1024 (one warp, every
+// lane returns it): the middle of the first bin at which the cumulative count
+// per sampled point reaches K (scaled to the subset), or range if none.  Lane
+// l sums bins [32 l, 32 l + 32), a warp prefix sum finds the lane whose chunk
+// crosses the target, that lane finds the bin (integer sums: exact).
+__device__ float params_pick(const unsigned *h, float range, const ParamsIn &in, int lane)
+{
+    const double target = (double)in.K * (double)in.S * (double)in.m / (double)(in.n - 1);
+    unsigned long long own = 0;
+    for (int b = 0; b < 32; ++b) own += h[lane * 32 + b];
+    unsigned long long inc = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const unsigned cross = __ballot_sync(FULL, (double)inc >= target);
+    int pick = -1;
+    if (cross) {
+        const int src = __ffs(cross) - 1;
+        if (lane == src) {
+            unsigned long long cum = inc - own;
+            for (int b = 0; b < 32; ++b) {
+                cum += h[lane * 32 + b];
+                if ((double)cum >= target) {
+                    pick = lane * 32 + b;
+                    break;
+                }
+            }
+        }
+        pick = __shfl_sync(FULL, pick, src);
+    }
+    return pick >= 0 ? (pick + 0.5f) * (range / 1024.0f) : range;
+}
+
 // Histogram of distances from the S sample points to the m subset points,
 // bins of width range / 1024 over [0, range), where range = eps_mean (stage
 // 0) or twice the stage-0 estimate (stage 1).  A thread holds one subset
@@ -173,14 +246,33 @@ __device__ __forceinline__ void sample_slice(int64_t S, int64_t &i0, int64_t &i1
 // memory); the block's histogram is added to the global one.
 template <int P>
 __global__ void k_eps_hist(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n,
-                           int64_t S, int64_t m, const GridParams *gp, PrepReduce *red, int stage)
+                           int64_t S, int64_t m, GridParams *gp, PrepReduce *red, int stage, const ParamsIn in)
 {
     __shared__ unsigned h[1024];
     __shared__ float4 sp[256 * 2];
+    __shared__ float s_range;
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) h[i] = 0;
     for (int i = threadIdx.x; i < (int)S * 2; i += blockDim.x) sp[i] = ((const float4 *)srow)[i];
+    // the grid parameters this stage needs, formed by every block (block
+    // (0, 0) also stores them for the kernels after): stage 0, the
+    // grid-independent fields and eps_mean; stage 1, the first eps_min
+    // estimate from the stage-0 histogram
+    const bool first = blockIdx.x == 0 && blockIdx.y == 0;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        float range;
+        if (stage == 0) {
+            range = eps_mean_of(red);
+            if (first && lane == 0) params_stage0(red, in, gp);
+        } else {
+            const float e = params_pick(red->hist[0], gp->eps_mean, in, lane);
+            if (first && lane == 0) gp->eps_min = e;
+            range = 2.0f * e;
+        }
+        if (lane == 0) s_range = range;
+    }
     __syncthreads();
-    const float range = stage == 0 ? gp->eps_mean : 2.0f * gp->eps_min;
+    const float range = s_range;
     if (range > 0.0f) {
         const float inv_bw = 1024.0f / range, r2 = below_bound(range);
         const int64_t sstride = n / S, mstride = n / m;
@@ -206,14 +298,6 @@ __global__ void k_eps_hist(const float *__restrict__ srow, const float *__restri
         if (h[i]) atomicAdd(&red->hist[stage][i], h[i]);
 }
 
-struct ParamsIn {
-    int64_t n;
-    int d, K;
-    int64_t S, m;        // histogram samples / subset size
-    float width_mult;    // cell side = width_mult * eps_min
-    int start_level;
-    int max_finer;       // cap on levels finer than the search-distance width
-};
 
 // Density skew: neighbours of each sampled point among the subset within
 // the radius where about K are expected (eps_min scaled by (n/m)^(1/d)).
@@ -221,14 +305,28 @@ struct ParamsIn {
 // samples; per sample, a warp ballot counts its lanes within the radius.
 template <int P>
 __global__ void k_eps_count(const float *__restrict__ srow, const float *__restrict__ mrow, int64_t n, int d,
-                            int64_t S, int64_t m, const GridParams *gp, PrepReduce *red)
+                            int64_t S, int64_t m, GridParams *gp, PrepReduce *red, const ParamsIn in)
 {
     __shared__ unsigned cnt[256];
     __shared__ float4 sp[256 * 2];
+    __shared__ float s_eps;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
     for (int i = threadIdx.x; i < (int)S * 2; i += blockDim.x) sp[i] = ((const float4 *)srow)[i];
+    // stage 2 of the grid parameters, formed by every block (block 0 also
+    // stores it): eps_min refined from the stage-1 histogram over [0, 2 x
+    // the first estimate), or eps_mean when that estimate is 0.  The first
+    // estimate is formed again here from the stage-0 histogram, since block
+    // 0 overwrites gp->eps_min
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const float range = 2.0f * params_pick(red->hist[0], gp->eps_mean, in, lane);
+        float e = params_pick(red->hist[1], range, in, lane);
+        if (!(range > 0.0f)) e = gp->eps_mean;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && lane == 0) gp->eps_min = e;
+        if (lane == 0) s_eps = e;
+    }
     __syncthreads();
-    const float e = gp->eps_min * powf((float)n / (float)m, 1.0f / (float)d);
+    const float e = s_eps * powf((float)n / (float)m, 1.0f / (float)d);
     if (e > 0.0f && isfinite(e)) {
         const float e2 = below_bound(e);
         const int64_t sstride = n / S, mstride = n / m;
@@ -269,27 +367,8 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
 {
     const int lane = threadIdx.x & 31;
     if (blockIdx.x || threadIdx.x >= 32) return;
-    const int d = in.d;
     if (stage == 0) {
-        if (lane) return;
-        gp->n = (int)in.n;
-        gp->d = d;
-        gp->K = in.K;
-        gp->nonfinite = red->nonfinite;
-        for (int k = 0; k < d; ++k) {
-            gp->lo[k] = fdec(red->lo_enc[k]);
-            gp->hi[k] = fdec(red->hi_enc[k]);
-        }
-        if (red->max_msb < red->min_lsb) {  // every coordinate is zero
-            gp->fixed_ok = 1;
-            gp->F = 0;
-        } else {
-            int F = -red->min_lsb;
-            gp->F = F;
-            gp->fixed_ok = (red->max_msb + F <= 29) ? 1 : 0;
-        }
-        gp->eps_mean = red->eps_pairs ? (float)(red->eps_sum / (double)red->eps_pairs) : 0.0f;
-        gp->eps_min = 0.0f;
+        if (lane == 0) params_stage0(red, in, gp);
         return;
     }
     if (stage == 3) {
@@ -307,43 +386,10 @@ __global__ void k_params(const PrepReduce *red, GridParams *gp, ParamsIn in, int
         if (lane == 0) k_params_grid(red, gp, in, (double)cs, cm);
         return;
     }
-    // the first bin at which the cumulative count per sampled point reaches
-    // K (scaled to the subset): lane l sums bins [32 l, 32 l + 32), a warp
-    // prefix sum finds the lane whose chunk crosses the target, that lane
-    // finds the bin
-    const unsigned *h = red->hist[stage - 1];
     const float range = stage == 1 ? gp->eps_mean : 2.0f * gp->eps_min;
-    const double target = (double)in.K * (double)in.S * (double)in.m / (double)(in.n - 1);
-    unsigned long long own = 0;
-    for (int b = 0; b < 32; ++b) own += h[lane * 32 + b];
-    unsigned long long inc = own;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
-    }
-    const unsigned cross = __ballot_sync(FULL, (double)inc >= target);
-    int pick = -1;
-    if (cross) {
-        const int src = __ffs(cross) - 1;
-        if (lane == src) {
-            unsigned long long cum = inc - own;
-            for (int b = 0; b < 32; ++b) {
-                cum += h[lane * 32 + b];
-                if ((double)cum >= target) {
-                    pick = lane * 32 + b;
-                    break;
-                }
-            }
-        }
-        pick = __shfl_sync(FULL, pick, src);
-    }
+    float eps = params_pick(red->hist[stage - 1], range, in, lane);
     if (lane) return;
-    float eps = pick >= 0 ? (pick + 0.5f) * (range / 1024.0f) : range;
-    if (stage == 1) {
-        gp->eps_min = eps;
-        return;
-    }
-    if (!(range > 0.0f)) eps = gp->eps_mean;
+    if (stage == 2 && !(range > 0.0f)) eps = gp->eps_mean;
     gp->eps_min = eps;
 }
 

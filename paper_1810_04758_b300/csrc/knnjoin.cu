@@ -983,17 +983,16 @@ void Pipeline::run(const float *pts_in, int64_t n, int d, int K, int32_t *ids_in
         // fill the GPU at m = 65,536)
         const dim3 gm((unsigned)((pin.m + 255) / 256), 4);
         const bool p4 = d <= 4;  // rows compared over 4 floats, else 8
-        k_params<<<1, 32, 0, s>>>(red, gp, pin, 0); ++launches;
-        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0);
-        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0);
+        // parameter stages 0-2 are formed inside the histogram kernels (each
+        // block from the reductions before it), stage 3 after the counts
+        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0, pin);
+        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 0, pin);
         ++launches;
-        k_params<<<1, 32, 0, s>>>(red, gp, pin, 1); ++launches;
-        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1);
-        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1);
+        if (p4) k_eps_hist<4><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1, pin);
+        else k_eps_hist<8><<<gm, 256, 0, s>>>(srow, mrow, n, pin.S, pin.m, gp, red, 1, pin);
         ++launches;
-        k_params<<<1, 32, 0, s>>>(red, gp, pin, 2); ++launches;
-        if (p4) k_eps_count<4><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red);
-        else k_eps_count<8><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red);
+        if (p4) k_eps_count<4><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, pin);
+        else k_eps_count<8><<<gm, 256, 0, s>>>(srow, mrow, n, d, pin.S, pin.m, gp, red, pin);
         ++launches;
         k_params<<<1, 32, 0, s>>>(red, gp, pin, 3); ++launches;
         CK(cudaGetLastError());
