@@ -2,11 +2,13 @@
 //
 // A join runs on one CUDA stream:
 //   a1 k_prep (data, and queries for R x S) -> a2 k_eps_pairs, k_eps_rows,
-//   k_eps_hist x2, k_eps_count, k_params x4 -> a3 k_keys -> a4 radix sort ->
-//   a5 k_gather -> pass loop { level cells + hash map, groups of the active
-//   queries, density order, work items, a7-a11 k_scan2 (k_scan for buffer
-//   overflows), compaction of the uncertified queries } until no query is
-//   left -> k_sqrt_rows -> result copy to the host if the outputs live there.
+//   k_eps_hist x2, k_eps_count (parameter stages 0-2 inside them), k_params
+//   -> a3 k_keys -> a4 radix sort -> a5 k_gather -> pass loop { level cell
+//   tables (dense or hash map), groups of the active queries, density order,
+//   work items, a7-a11 k_scan2 (k_scan for buffer overflows), compaction of
+//   the uncertified queries; the last few by the brute-force tail of
+//   tail.cuh } until no query is left -> k_sqrt_rows -> result copy to the
+//   host if the outputs live there.
 // The pass loop is the device re-queue of Alg. 1 (failed queries go back to
 // the queue); each pass scans a ring of cells twice as wide as the last.
 // Variants on the same loop: R x S (queries with their own keys and order),
